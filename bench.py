@@ -1,0 +1,391 @@
+#!/usr/bin/env python3
+"""Benchmark: Contour connected components (MM^h sweeps) on GB300.
+
+Default workload: R-MAT scale 24 (16,777,216 vertices, 268,435,456 edges,
+a/b/c/d = .57/.19/.19/.05, permuted ids), operator order 2, asynchronous,
+convergence check every sweep -- the paper's default C-2 variant.  One step
+is one complete ``cc_run`` (label init, sweeps to convergence, compress) on a
+device-resident graph.
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the CPU oracle
+(serial union-find) on the host instead.  Under torchrun every rank solves
+its own replica graph (weak scaling, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import torch  # noqa: E402
+
+import graphgen as gg  # noqa: E402
+
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--workload", default="rmat24", choices=["rmat24", "grid4096", "components64"])
+    p.add_argument("--order", type=int, default=2)
+    p.add_argument("--mode", choices=["async", "sync"], default="async")
+    p.add_argument("--interval", type=int, default=1)
+    p.add_argument("--no-variants", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--cpu-seconds", type=float, default=12.0)
+    return p.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# distributed plumbing (replicas only)
+# ---------------------------------------------------------------------------
+
+def dist_init():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+    elif torch.cuda.is_available():
+        torch.cuda.set_device(0)
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch.distributed as dist
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+# workloads
+# ---------------------------------------------------------------------------
+
+def make_workload(name: str, device, seed: int):
+    if name == "rmat24":
+        s, d = gg.rmat(24, seed=seed, device=device)
+        return (1 << 24), s, d, {"workload": "rmat-scale24", "graph": "R-MAT a/b/c/d=.57/.19/.19/.05, edge factor 16, ids permuted"}
+    if name == "grid4096":
+        s, d = gg.grid(4096, 4096, seed=seed, device=device)
+        return 4096 * 4096, s, d, {"workload": "grid-4096x4096", "graph": "4-neighbour grid, 5% edges deleted, ids permuted"}
+    n, s, d = gg.components64(seed=seed, device=device)
+    return n, s, d, {"workload": "components64", "graph": "32 paths + 32 ER(deg 8)+spanning path, 1024 vertices each"}
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap,utilization.gpu")
+
+    def __init__(self, local_rank: int):
+        self.proc = None
+        self.index = self._physical_index(local_rank)
+
+    @staticmethod
+    def _physical_index(local_rank):
+        vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+        if vis:
+            parts = [p.strip() for p in vis.split(",") if p.strip()]
+            if local_rank < len(parts) and parts[local_rank].isdigit():
+                return parts[local_rank]
+        return str(local_rank)
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", self.index, f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        rows = []
+        for line in out.splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                rows.append((float(f[0]), float(f[1]), f[3:7], float(f[7]) if f[7] not in ("", "[N/A]") else 0.0))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        loaded = [r for r in rows if r[3] > 0] or rows
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in loaded for i, v in enumerate(r[2]) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in loaded), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(loaded)}
+
+
+# ---------------------------------------------------------------------------
+# CPU baseline (the oracle, as it stands)
+# ---------------------------------------------------------------------------
+
+def cpu_oracle_rate(n, s_host, d_host, target_s: float):
+    """Serial union-find on a prefix of the edge list sized to ~target_s seconds."""
+    import oracle
+    oracle.build()
+    m = s_host.numel()
+    probe = max(1, m // 64)
+    t0 = time.perf_counter()
+    oracle.uf_labels(n, s_host[:probe], d_host[:probe])
+    dt = max(time.perf_counter() - t0, 1e-6)
+    k = int(min(m, probe * max(1.0, target_s / dt)))
+    t0 = time.perf_counter()
+    oracle.uf_labels(n, s_host[:k], d_host[:k])
+    dt = time.perf_counter() - t0
+    return k / dt, k, dt
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    n, s, d, cfg = make_workload(args.workload, dev, gg.BASE_SEED)
+    s_h, d_h = s.cpu(), d.cpu()
+    del s, d
+    m = s_h.numel()
+    per_step = max(2.0, min(args.cpu_seconds, 150.0 / max(1, args.steps + args.warmup)))
+    rates = []
+    for i in range(args.warmup + args.steps):
+        r, k, dt = cpu_oracle_rate(n, s_h, d_h, per_step)
+        if i >= args.warmup:
+            rates.append((r, k, dt))
+    tot_edges = sum(k for _, k, _ in rates)
+    tot_t = sum(dt for _, _, dt in rates)
+    value = tot_edges / tot_t
+    sample = f"serial union-find over the first {rates[-1][1]:,} of {m:,} edges (all {n:,} vertices) per step"
+    cfg.update(n=n, m=m, ids="int32")
+    line = {"impl": "reference", "metric": "CC edges/sec (m / solve time)", "value": value,
+            "unit": "edges/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * tot_t / len(rates), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int32", "data": "synthetic", "config": cfg,
+            "cpu_baseline": {"value": value, "unit": "edges/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "edges/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+
+def _traffic_for(kernel: str):
+    """DRAM bytes per launch from the committed ncu summary, if it matches the source."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    src = os.path.join(ROOT, "paper_2311_02811_gb300", "csrc", "mm_kernels.cuh")
+    try:
+        rec = json.load(open(path))
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+        ent = rec.get(kernel)
+        if ent and ent.get("source_sha256") == sha:
+            return ent.get("dram_bytes_per_launch")
+    except (OSError, ValueError):
+        pass
+    return None
+
+
+def _peaks():
+    try:
+        pk = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        return float(pk["hbm_gbs"]), "measured"
+    except (OSError, ValueError, KeyError):
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def timed_runs(cc, g, out, n_steps, order, mode, interval, stream):
+    stats = []
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(n_steps):
+        stats.append(cc.cc_run(g, out, order, mode, interval))
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    return ev0.elapsed_time(ev1), stats
+
+
+def run_ours(args, rank, world, local):
+    import paper_2311_02811_gb300 as cc
+    assert torch.cuda.is_available(), "bench needs a CUDA device"
+    dev = torch.device("cuda", torch.cuda.current_device())
+    mode = cc.CC_ASYNC if args.mode == "async" else cc.CC_SYNC
+    seed = gg.BASE_SEED + rank
+    n, s, d, cfg = make_workload(args.workload, dev, seed)
+    m = s.numel()
+    stream = torch.cuda.current_stream()
+    g = cc.cc_init(n, s, d, stream=stream.cuda_stream)
+    out = torch.empty(n, dtype=torch.int32, device=dev)
+    for _ in range(args.warmup):
+        cc.cc_run(g, out, args.order, mode, args.interval)
+    torch.cuda.synchronize()
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    barrier(world)
+    torch.cuda.synchronize()
+    ms, stats = timed_runs(cc, g, out, args.steps, args.order, mode, args.interval, stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    clocks = sampler.stop()
+    ms_max = max_over_ranks(ms, world)
+    value = m * args.steps * world / (ms_max * 1e-3)
+
+    sweeps = [st.sweeps for st in stats]
+    loop_ms = sum(st.loop_ms for st in stats)
+    tot_sweeps = sum(sweeps)
+    B = 4
+    per_sweep = 2 * B * m + B * n + (3 * B * n if mode == cc.CC_SYNC else 0)
+    sweep_ms = loop_ms / max(1, tot_sweeps)
+    achieved = per_sweep / (sweep_ms * 1e-3) / 1e9
+    peak, peak_kind = _peaks()
+    kname = f"mm_sweep_kernel<{args.order},{'sync' if mode == cc.CC_SYNC else 'async'},int32>"
+    launches_per_run = [3 + sw * (2 if mode == cc.CC_SYNC else 1) + sw // args.interval for sw in sweeps]
+
+    line = {
+        "metric": "CC edges/sec (m / solve time)", "value": value, "unit": "edges/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": dict(cfg, n=n, m=m, order=args.order, mode=args.mode, check_interval=args.interval,
+                       ids="int32", parallelism=f"replicas x{world}" if world > 1 else "single GPU",
+                       l2="inputs larger than L2: edge list %.2f GB streamed every sweep" % (8 * m / 1e9),
+                       sweeps_per_step=statistics.median(sweeps)),
+        "roofline": {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak,
+                     "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": _traffic_for(kname),
+                     "alg_bytes_per_launch": per_sweep,
+                     "launch_ms": sweep_ms,
+                     "timing": "sweep-loop CUDA events on the launching stream / sweeps (includes the per-block check kernel)"},
+        "clocks": clocks,
+        "gpu_launches": sum(launches_per_run),
+    }
+
+    if not args.no_e2e:
+        line["e2e"] = e2e(cc, n, s, d, args, mode, world, stream)
+
+    if not args.no_variants and rank == 0:
+        line["variants"] = variants(cc, g, out, n, m, args, dev, seed, stream)
+
+    cc.cc_free(g)
+
+    if rank == 0 and world == 1 and not args.no_cpu:
+        s_h, d_h = s.cpu(), d.cpu()
+        rate, k, dt = cpu_oracle_rate(n, s_h, d_h, args.cpu_seconds)
+        line["cpu_baseline"] = {"value": rate, "unit": "edges/s", "cores": 1, "kind": "oracle",
+                                "sample": f"serial union-find over the first {k:,} of {m:,} edges "
+                                          f"(all {n:,} vertices), {dt:.1f} s"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def e2e(cc, n, s, d, args, mode, world, stream):
+    """Same metric through the public API from pinned host buffers, copies included."""
+    s_h = s.cpu().pin_memory()
+    d_h = d.cpu().pin_memory()
+    out_h = torch.empty(n, dtype=torch.int32).pin_memory()
+    m = s_h.numel()
+
+    def one():
+        g = cc.cc_init(n, s_h, d_h, on_device=False, stream=stream.cuda_stream)
+        cc.cc_run(g, out_h, args.order, mode, args.interval, out_on_device=False)
+        cc.cc_free(g)
+
+    one()
+    steps = max(1, min(args.steps, 5))
+    torch.cuda.synchronize()
+    barrier(world)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(steps):
+        one()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = max_over_ranks(ev0.elapsed_time(ev1), world)
+    return {"value": m * steps * world / (ms * 1e-3), "unit": "edges/s",
+            "h2d_bytes_per_step": 2 * 4 * m, "d2h_bytes_per_step": 4 * n, "steps": steps,
+            "ms_per_step": ms / steps}
+
+
+def variants(cc, g, out, n, m, args, dev, seed, stream):
+    res = {}
+
+    def measure(gh, o, nn, mm, order, mode, c, reps=3):
+        cc.cc_run(gh, o, order, mode, c)
+        ms, st = timed_runs(cc, gh, o, reps, order, mode, c, stream)
+        return {"edges_per_s": mm * reps / (ms * 1e-3), "ms": ms / reps, "sweeps": st[-1].sweeps,
+                "loop_ms": st[-1].loop_ms}
+
+    for order, mode, name in [(2, cc.CC_SYNC, "o2-sync"), (4, cc.CC_ASYNC, "o4-async"),
+                              (4, cc.CC_SYNC, "o4-sync"), (0, cc.CC_ASYNC, "full-async"),
+                              (1, cc.CC_ASYNC, "o1-async")]:
+        res[f"{args.workload}/{name}"] = measure(g, out, n, m, order, mode, 1)
+    if args.workload != "grid4096":
+        n2, s2, d2, _ = make_workload("grid4096", dev, seed)
+        g2 = cc.cc_init(n2, s2, d2, stream=stream.cuda_stream)
+        o2 = torch.empty(n2, dtype=torch.int32, device=dev)
+        for order, mode, name in [(2, cc.CC_ASYNC, "o2-async"), (2, cc.CC_SYNC, "o2-sync"),
+                                  (4, cc.CC_ASYNC, "o4-async"), (0, cc.CC_ASYNC, "full-async")]:
+            res[f"grid4096/{name}"] = measure(g2, o2, n2, s2.numel(), order, mode, 1)
+        cc.cc_free(g2)
+    return res
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_init()
+    try:
+        if args.impl == "reference":
+            run_reference(args, rank, world)
+        else:
+            run_ours(args, rank, world, local)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

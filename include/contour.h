@@ -1,0 +1,162 @@
+/*
+ * contour.h -- C ABI of libcontour.so, a GB300 (sm_103a) connected-components
+ * library built around the minimum-mapping operator of the Contour algorithm
+ * (Du, Alvarado Rodriguez, Li, Dindoost, Bader: "Contour Algorithm for
+ * Connectivity", arXiv 2311.02811).
+ *
+ * Problem (Section II-A): an undirected graph with vertex ids 0..n-1 and m
+ * edges <w, v>.  Every entry point that returns labels returns, for each
+ * vertex v, the smallest vertex id of v's connected component.  That value is
+ * the unique fixed point reached by Alg. 1 and by its asynchronous variant
+ * (Section III-B1): labels only ever decrease to values taken from the same
+ * component, and a state in which no edge can lower a label consists of stars
+ * whose roots are component minima (Section II-A).
+ *
+ * Conventions shared by every call:
+ *   - No call throws; each returns a cc_status.  cc_last_error() gives a
+ *     human-readable detail string for the calling host thread.
+ *   - "Device" pointers are CUDA device (or managed) pointers of the current
+ *     device; "host" pointers may be pageable or pinned.
+ *   - Work is enqueued on the caller's CUDA stream (cudaStream_t passed as
+ *     void*; NULL means the legacy default stream).  Calls that return labels
+ *     to the host, or that report a status computed on the device, synchronise
+ *     that stream before returning.
+ *   - A cc_graph handle may be used by one host thread at a time.
+ *   - id_bits selects the vertex-id type: CC_ID32 (int32_t, n < 2^31) or
+ *     CC_ID64 (int64_t).  Edge counts and offsets are always int64_t.
+ */
+#ifndef CONTOUR_H
+#define CONTOUR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct cc_graph cc_graph; /* opaque; owned by the library */
+
+typedef enum {
+    CC_OK = 0,
+    CC_EINVAL = 1,        /* bad argument (NULL pointer, n < 0, bad enum, bad snapshot) */
+    CC_EIDRANGE = 2,      /* an edge endpoint lies outside [0, n) */
+    CC_ENOMEM = 3,        /* device or pinned-host allocation failed */
+    CC_ECUDA = 4,         /* a CUDA runtime call failed (detail in cc_last_error) */
+    CC_ENOTCONVERGED = 5, /* max_sweeps reached; labels are a valid partial state */
+    CC_ETIMEOUT = 6       /* a bounded device-side wait gave up (batched launch) */
+} cc_status;
+
+enum { CC_ID32 = 32, CC_ID64 = 64 };
+enum { CC_COO = 0, CC_CSR = 1 };
+enum { CC_SYNC = 0, CC_ASYNC = 1 };
+/* Operator order: h >= 1 is MM^h of Def. 3; CC_ORDER_FULL follows each label
+ * chain to its root (at most 1024 hops, the "C-m" variant with m = 1024 of
+ * Section III-B4); CC_ORDER_AUTO lets the learned scheduler choose. */
+enum { CC_ORDER_FULL = 0, CC_ORDER_AUTO = -1 };
+enum { CC_MAX_ORDER = 1024 };
+
+typedef struct {
+    int32_t sweeps;         /* edge sweeps executed (whole check blocks)            */
+    int32_t order;          /* operator order used (CC_ORDER_FULL for full chain)   */
+    int32_t mode;           /* CC_SYNC or CC_ASYNC                                  */
+    int32_t check_interval; /* sweeps per convergence check                         */
+    double solve_ms;        /* device time from label init to final compress        */
+    double edges_per_s;     /* m / solve time                                       */
+    double alg_bytes;       /* algorithmic bytes moved by all sweeps (see below)    */
+    double loop_ms;         /* device time of the sweep loop alone: every sweep, the */
+                            /* L = L_u copies and the one-thread check per block    */
+} cc_stats;
+
+/*
+ * cc_init -- build a graph handle.
+ *
+ * Section II-A: vertex ids are 0..n-1; the graph is given either as
+ *   layout == CC_COO: a = src[m], b = dst[m], m = m_or_nnz undirected edges
+ *                     <src[e], dst[e]> (self-loops and repeats allowed), or
+ *   layout == CC_CSR: a = int64_t offsets[n+1], b = cols[nnz], nnz = m_or_nnz;
+ *                     every stored entry (r, cols[k]) becomes one edge.  A
+ *                     symmetric CSR therefore yields every edge twice.
+ * Ids have the type chosen by id_bits.
+ *
+ * on_device == 0: a and b are host arrays; they are copied to the device and
+ *                 may be freed after the call returns.
+ * on_device == 1: a and b are device arrays.  A COO pair whose pointers are
+ *                 16-byte aligned is borrowed (no copy) and must stay alive
+ *                 and unchanged until cc_free; otherwise it is copied.
+ *
+ * Every id is checked on the device: CC_EIDRANGE if any endpoint lies
+ * outside [0, n) (CSR: also CC_EINVAL for offsets that are not a
+ * non-decreasing sequence from 0 to nnz).  n == 0 and m == 0 are valid.
+ * On success *g owns its device buffers until cc_free(*g).
+ */
+cc_status cc_init(cc_graph **g, int64_t n, int id_bits, int layout, const void *a,
+                  const void *b, int64_t m_or_nnz, int on_device, void *cuda_stream);
+
+/*
+ * cc_run -- label every vertex with the smallest id of its component.
+ *
+ * Runs the Contour iteration of Alg. 1 on the device: labels L[i] = i
+ * (Alg. 1 initialisation) or a resume snapshot, then repeated sweeps in
+ * which every edge <w, v> applies the order-h minimum-mapping operator of
+ * Def. 3: z = min(L^h[w], L^h[v]) and every chain entry L[w], L[L[w]], ...,
+ * L[L^{h-1}[w]] (and the same for v) that is larger than z is set to z
+ * (conditional assignment, Def. 1).
+ *
+ *   order           h >= 1, CC_ORDER_FULL, or CC_ORDER_AUTO (learned scheduler;
+ *                   the plain order-2 synchronous schedule when no weights are
+ *                   loaded).  h is at most CC_MAX_ORDER.
+ *   mode            CC_SYNC: Alg. 1 literally -- reads from L, atomic-min
+ *                   writes into the update array L_u (Eq. "cas"), then L = L_u;
+ *                   every sweep is deterministic.  CC_ASYNC: in-place plain
+ *                   stores into L (Section III-B1 and III-B3).
+ *   check_interval  c >= 1: the convergence flag of Section III-B2 is taken
+ *                   from the last sweep of every block of c sweeps; the run
+ *                   stops after the first block whose last sweep saw no edge
+ *                   whose chain could lower a label.  With CC_ORDER_AUTO a
+ *                   value of 0 lets the scheduler choose c as well.
+ *   max_sweeps      >= 1; the run stops after this many sweeps (rounded up to
+ *                   whole blocks) and returns CC_ENOTCONVERGED, leaving a
+ *                   valid partial state in labels_out that a later call can
+ *                   resume from.
+ *   init_labels     NULL, or n ids to start from (a snapshot of an earlier
+ *                   run).  Each entry must satisfy 0 <= init[x] <= x, else
+ *                   CC_EINVAL.  Same memory space as labels_out.
+ *   labels_out      n ids (id_bits wide), caller-allocated; device memory when
+ *                   out_on_device != 0, else host memory.
+ *   stats           NULL or filled on return (also on CC_ENOTCONVERGED).
+ *
+ * After a converged loop a compress pass sets L[x] to the root of its chain
+ * and counts the labels it moves: the result is a set of stars (Section II-A)
+ * and at a true fixed point nothing moves (a moved label is reported as
+ * CC_ECUDA, an internal error).  A run that stops at max_sweeps is returned
+ * exactly as its last sweep left it.  Work is enqueued on the handle's stream (cc_init's stream, or the
+ * one set by cc_graph_set_stream), which cc_run synchronises before returning.
+ *
+ * Algorithmic bytes per sweep (stats.alg_bytes): async 2*B*m + B*n, sync adds
+ * 3*B*n (L_u writes and the L = L_u copy), B = id_bits / 8.
+ */
+cc_status cc_run(cc_graph *g, int order, int mode, int check_interval, int32_t max_sweeps,
+                 const void *init_labels, void *labels_out, int out_on_device, cc_stats *stats);
+
+/* Make later cc_run calls on g enqueue on another stream (default: the stream
+ * passed to cc_init). */
+cc_status cc_graph_set_stream(cc_graph *g, void *cuda_stream);
+
+/* Number of vertices and stored edges of a handle (either may be NULL). */
+cc_status cc_graph_info(const cc_graph *g, int64_t *n, int64_t *m);
+
+/* Release a handle and every device buffer it owns.  NULL is ignored. */
+void cc_free(cc_graph *g);
+
+/* Static description of a status code. */
+const char *cc_strerror(cc_status s);
+
+/* Detail message of the last failing call on this host thread ("" if none). */
+const char *cc_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CONTOUR_H */

@@ -1,0 +1,182 @@
+"""Python binding of libcontour.so (C ABI in include/contour.h).
+
+The functions below carry the C entry points' names and only marshal
+arguments: every step of the computation runs in the CUDA library.  Arrays may
+be torch tensors (CPU or CUDA) or numpy arrays; device tensors are passed by
+pointer, and the stream defaults to torch's current CUDA stream.
+
+The library must have been built (``paper_2311_02811_gb300.build.build()`` or
+``__graft_entry__.build()``); importing this module raises ImportError when
+libcontour.so is missing, and there is no fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+__all__ = [
+    "CC_OK", "CC_EINVAL", "CC_EIDRANGE", "CC_ENOMEM", "CC_ECUDA", "CC_ENOTCONVERGED",
+    "CC_ETIMEOUT", "CC_ID32", "CC_ID64", "CC_COO", "CC_CSR", "CC_SYNC", "CC_ASYNC",
+    "CC_ORDER_FULL", "CC_ORDER_AUTO", "CCError", "cc_stats", "cc_graph", "lib", "LIB_PATH",
+    "cc_init", "cc_run", "cc_free", "cc_graph_info", "cc_graph_set_stream", "cc_strerror",
+    "cc_last_error",
+]
+
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libcontour.so")
+
+CC_OK, CC_EINVAL, CC_EIDRANGE, CC_ENOMEM, CC_ECUDA, CC_ENOTCONVERGED, CC_ETIMEOUT = range(7)
+CC_ID32, CC_ID64 = 32, 64
+CC_COO, CC_CSR = 0, 1
+CC_SYNC, CC_ASYNC = 0, 1
+CC_ORDER_FULL, CC_ORDER_AUTO = 0, -1
+
+
+class cc_stats(ctypes.Structure):
+    _fields_ = [("sweeps", ctypes.c_int32), ("order", ctypes.c_int32), ("mode", ctypes.c_int32),
+                ("check_interval", ctypes.c_int32), ("solve_ms", ctypes.c_double),
+                ("edges_per_s", ctypes.c_double), ("alg_bytes", ctypes.c_double),
+                ("loop_ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class CCError(RuntimeError):
+    """A libcontour call returned a status other than CC_OK."""
+
+    def __init__(self, status, where, detail, stats=None):
+        super().__init__(f"{where}: {cc_strerror(status)} ({detail})")
+        self.status = status
+        self.stats = stats
+
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is not built; run paper_2311_02811_gb300.build.build() "
+                      "(needs nvcc); there is no CPU fallback")
+
+lib = ctypes.CDLL(LIB_PATH)
+_p, _i64, _i32, _int = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int
+lib.cc_init.argtypes = [ctypes.POINTER(_p), _i64, _int, _int, _p, _p, _i64, _int, _p]
+lib.cc_init.restype = _int
+lib.cc_run.argtypes = [_p, _int, _int, _int, _i32, _p, _p, _int, ctypes.POINTER(cc_stats)]
+lib.cc_run.restype = _int
+lib.cc_graph_info.argtypes = [_p, ctypes.POINTER(_i64), ctypes.POINTER(_i64)]
+lib.cc_graph_info.restype = _int
+lib.cc_graph_set_stream.argtypes = [_p, _p]
+lib.cc_graph_set_stream.restype = _int
+lib.cc_free.argtypes = [_p]
+lib.cc_free.restype = None
+lib.cc_strerror.argtypes = [_int]
+lib.cc_strerror.restype = ctypes.c_char_p
+lib.cc_last_error.argtypes = []
+lib.cc_last_error.restype = ctypes.c_char_p
+
+
+def cc_strerror(status: int) -> str:
+    return lib.cc_strerror(status).decode()
+
+
+def cc_last_error() -> str:
+    return lib.cc_last_error().decode()
+
+
+def _check(status, where, stats=None):
+    if status != CC_OK:
+        raise CCError(status, where, cc_last_error(), stats)
+
+
+def _ptr(x):
+    """(pointer, on_device) of a torch tensor / numpy array / None / int."""
+    if x is None:
+        return None, False
+    if isinstance(x, int):
+        return x, False
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("arrays must be contiguous")
+        return x.data_ptr(), x.device.type == "cuda"
+    if hasattr(x, "ctypes"):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("arrays must be contiguous")
+        return x.ctypes.data, False
+    raise TypeError(f"unsupported array type {type(x)}")
+
+
+def _stream(stream):
+    if stream is not None:
+        return int(stream)
+    import torch
+    if torch.cuda.is_available():
+        return torch.cuda.current_stream().cuda_stream
+    return 0
+
+
+def _id_bits(x, default=CC_ID32):
+    dt = str(getattr(x, "dtype", ""))
+    if "int64" in dt:
+        return CC_ID64
+    if "int32" in dt:
+        return CC_ID32
+    return default
+
+
+class cc_graph:
+    """A cc_graph* handle.  Device arrays that cc_init may borrow are referenced
+    here so that Python keeps them alive until cc_free."""
+
+    def __init__(self, ptr, keep):
+        self._as_parameter_ = _p(ptr)
+        self._keep = keep
+
+    @property
+    def ptr(self):
+        return self._as_parameter_.value
+
+
+def cc_init(n, a, b, m=None, id_bits=None, layout=CC_COO, on_device=None, stream=None):
+    """Create a graph handle; see cc_init in contour.h."""
+    pa, da = _ptr(a)
+    pb, db = _ptr(b)
+    if m is None:
+        m = len(b) if b is not None else 0
+    if id_bits is None:
+        id_bits = _id_bits(b)
+    if on_device is None:
+        on_device = da or db
+    g = _p()
+    _check(lib.cc_init(ctypes.byref(g), int(n), int(id_bits), int(layout), pa, pb, int(m),
+                       int(bool(on_device)), _stream(stream)), "cc_init")
+    return cc_graph(g.value, (a, b) if on_device else ())
+
+
+def cc_run(g, labels_out, order=2, mode=CC_ASYNC, check_interval=1, max_sweeps=1 << 20,
+           init_labels=None, out_on_device=None, raise_on_error=True):
+    """Label every vertex with its component's minimum id; returns cc_stats."""
+    po, do = _ptr(labels_out)
+    pi, _ = _ptr(init_labels)
+    if out_on_device is None:
+        out_on_device = do
+    st = cc_stats()
+    rc = lib.cc_run(g, int(order), int(mode), int(check_interval), int(max_sweeps), pi, po,
+                    int(bool(out_on_device)), ctypes.byref(st))
+    if raise_on_error:
+        _check(rc, "cc_run", st)
+        return st
+    return rc, st
+
+
+def cc_graph_info(g):
+    n, m = _i64(), _i64()
+    _check(lib.cc_graph_info(g, ctypes.byref(n), ctypes.byref(m)), "cc_graph_info")
+    return n.value, m.value
+
+
+def cc_graph_set_stream(g, stream):
+    _check(lib.cc_graph_set_stream(g, int(stream)), "cc_graph_set_stream")
+
+
+def cc_free(g):
+    lib.cc_free(g)
+    if isinstance(g, cc_graph):
+        g._as_parameter_ = _p(None)
+        g._keep = ()

@@ -1,0 +1,563 @@
+// Host engine and C ABI of the single-graph Contour path (include/contour.h).
+//
+// cc_run enqueues, on the caller's stream:
+//   ctl reset -> label init (Alg. 1 initialisation, or a validated snapshot)
+//   -> one CUDA graph holding a conditional WHILE node whose body runs one
+//      check block (c sweeps, plus L = L_u after each synchronous sweep) and
+//      a one-thread check kernel that clears the flag and sets the loop
+//      condition (Section III-B2 early convergence check)
+//   -> compress -> labels / control block back to the caller.
+// The loop never returns to the host between sweeps.
+#include <cuda_runtime.h>
+
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/contour.h"
+#include "cc_internal.h"
+#include "mm_kernels.cuh"
+
+using cc::Ctl;
+
+// ---------------------------------------------------------------------------
+// errors
+// ---------------------------------------------------------------------------
+
+static thread_local std::string g_last_error;
+
+namespace cc {
+
+cc_status set_error(cc_status s, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return s;
+}
+
+cc_status cuda_fail(cudaError_t e, const char* what, const char* file, int line) {
+    cudaGetLastError();  // clear a sticky-free error so later calls are not poisoned
+    return set_error(e == cudaErrorMemoryAllocation ? CC_ENOMEM : CC_ECUDA, "%s failed at %s:%d: %s",
+                     what, file, line, cudaGetErrorString(e));
+}
+
+int device_sms() {
+    static int sms = 0;
+    if (sms == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms <= 0) sms = 1;
+    }
+    return sms;
+}
+
+// Persistent grid: blocks resident on every SM at once (occupancy-limited).
+int persistent_blocks(const void* fn, int threads, size_t smem) {
+    static std::mutex mu;
+    static std::unordered_map<const void*, int> cache;
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = cache.find(fn);
+    if (it != cache.end()) return it->second;
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, smem) != cudaSuccess ||
+        per_sm <= 0)
+        per_sm = 1;
+    const int blocks = per_sm * device_sms();
+    cache[fn] = blocks;
+    return blocks;
+}
+
+}  // namespace cc
+
+using cc::cuda_fail;
+using cc::set_error;
+
+#define CC_CUDA(expr)                                                   \
+    do {                                                                \
+        cudaError_t e_ = (expr);                                        \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #expr, __FILE__, __LINE__); \
+    } while (0)
+
+#define CC_LAUNCHED()                                                   \
+    do {                                                                \
+        cudaError_t e_ = cudaGetLastError();                            \
+        if (e_ != cudaSuccess) return cuda_fail(e_, "kernel launch", __FILE__, __LINE__); \
+    } while (0)
+
+// ---------------------------------------------------------------------------
+// handle
+// ---------------------------------------------------------------------------
+
+struct LoopGraph {
+    int order = 0, mode = 0, c = 0;
+    void* L = nullptr;
+    void* Lu = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+struct cc_graph {
+    int64_t n = 0, m = 0;
+    int id_bits = 32;
+    void* src = nullptr;
+    void* dst = nullptr;
+    bool own_edges = false;
+    void* L = nullptr;   // working labels when the caller's output is on the host
+    void* Lu = nullptr;  // update array of synchronous runs
+    Ctl* ctl = nullptr;
+    Ctl* ctl_h = nullptr;  // pinned mirror
+    cudaStream_t stream = nullptr;  // caller's stream (cc_init / cc_graph_set_stream)
+    cudaStream_t cap = nullptr;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr, evl0 = nullptr, evl1 = nullptr;
+    std::vector<LoopGraph> loops;
+};
+
+static size_t id_size(int id_bits) { return id_bits == 64 ? 8 : 4; }
+
+static void free_loops(cc_graph* g) {
+    for (auto& lg : g->loops) {
+        if (lg.exec) cudaGraphExecDestroy(lg.exec);
+        if (lg.graph) cudaGraphDestroy(lg.graph);
+    }
+    g->loops.clear();
+}
+
+static void destroy(cc_graph* g) {
+    if (!g) return;
+    free_loops(g);
+    if (g->own_edges) {
+        cudaFree(g->src);
+        cudaFree(g->dst);
+    }
+    cudaFree(g->L);
+    cudaFree(g->Lu);
+    cudaFree(g->ctl);
+    if (g->ctl_h) cudaFreeHost(g->ctl_h);
+    if (g->cap) cudaStreamDestroy(g->cap);
+    if (g->ev0) cudaEventDestroy(g->ev0);
+    if (g->ev1) cudaEventDestroy(g->ev1);
+    if (g->evl0) cudaEventDestroy(g->evl0);
+    if (g->evl1) cudaEventDestroy(g->evl1);
+    delete g;
+}
+
+static const int kThreads = 256;
+
+template <typename K>
+static int grid_for(K kernel, int64_t work_items) {
+    const int cap = cc::persistent_blocks(reinterpret_cast<const void*>(kernel), kThreads, 0);
+    int64_t need = (work_items + kThreads - 1) / kThreads;
+    if (need < 1) need = 1;
+    return (int)(need < cap ? need : cap);
+}
+
+// ---------------------------------------------------------------------------
+// sweep dispatch
+// ---------------------------------------------------------------------------
+
+template <int H, bool SYNC, typename IdT>
+static cudaError_t launch_sweep_t(const cc_graph* g, IdT* L, IdT* Lu, int h, int32_t* flag,
+                                  cudaStream_t s) {
+    constexpr int G = (H == 1) ? 2 : 1;  // edge groups of 4 per thread per step
+    auto k = cc::mm_sweep_kernel<H, SYNC, G, IdT>;
+    const int grid = grid_for(k, g->m / (4 * G) + 1);
+    k<<<grid, kThreads, 0, s>>>(static_cast<const IdT*>(g->src), static_cast<const IdT*>(g->dst),
+                                 g->m, L, Lu, h, flag);
+    return cudaGetLastError();
+}
+
+template <bool SYNC, typename IdT>
+static cudaError_t launch_sweep_m(const cc_graph* g, int order, IdT* L, IdT* Lu, int32_t* flag,
+                                  cudaStream_t s) {
+    switch (order) {
+        case 1: return launch_sweep_t<1, SYNC, IdT>(g, L, Lu, 1, flag, s);
+        case 2: return launch_sweep_t<2, SYNC, IdT>(g, L, Lu, 2, flag, s);
+        case 4: return launch_sweep_t<4, SYNC, IdT>(g, L, Lu, 4, flag, s);
+        case CC_ORDER_FULL: return launch_sweep_t<0, SYNC, IdT>(g, L, Lu, cc::kFullChainHops, flag, s);
+        default: return launch_sweep_t<0, SYNC, IdT>(g, L, Lu, order, flag, s);
+    }
+}
+
+template <typename IdT>
+static cudaError_t launch_copy(IdT* dst, const IdT* src, int64_t n, cudaStream_t s) {
+    auto k = cc::copy_kernel<IdT>;
+    const int per = 16 / (int)sizeof(IdT);
+    k<<<grid_for(k, n / per + 1), kThreads, 0, s>>>(dst, src, n);
+    return cudaGetLastError();
+}
+
+// One check block: c sweeps (the flag only from the last), then the check.
+template <typename IdT>
+static cudaError_t enqueue_block(cc_graph* g, int order, int mode, int c, IdT* L, IdT* Lu,
+                                 cudaGraphConditionalHandle loop, cudaStream_t s) {
+    for (int j = 0; j < c; ++j) {
+        int32_t* flag = (j == c - 1) ? &g->ctl->flag : nullptr;
+        cudaError_t e = (mode == CC_SYNC) ? launch_sweep_m<true, IdT>(g, order, L, Lu, flag, s)
+                                          : launch_sweep_m<false, IdT>(g, order, L, nullptr, flag, s);
+        if (e != cudaSuccess) return e;
+        if (mode == CC_SYNC) {
+            e = launch_copy<IdT>(L, Lu, g->n, s);
+            if (e != cudaSuccess) return e;
+        }
+    }
+    cc::check_kernel<<<1, 32, 0, s>>>(g->ctl, c, loop);
+    return cudaGetLastError();
+}
+
+static cc_status build_loop(cc_graph* g, int order, int mode, int c, void* L, void* Lu,
+                            LoopGraph* out) {
+    LoopGraph lg;
+    lg.order = order;
+    lg.mode = mode;
+    lg.c = c;
+    lg.L = L;
+    lg.Lu = Lu;
+    CC_CUDA(cudaGraphCreate(&lg.graph, 0));
+    cudaGraphConditionalHandle loop;
+    cudaError_t e = cudaGraphConditionalHandleCreate(&loop, lg.graph, 1, cudaGraphCondAssignDefault);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(lg.graph);
+        return cuda_fail(e, "cudaGraphConditionalHandleCreate", __FILE__, __LINE__);
+    }
+    cudaGraphNodeParams p = {};
+    p.type = cudaGraphNodeTypeConditional;
+    p.conditional.handle = loop;
+    p.conditional.type = cudaGraphCondTypeWhile;
+    p.conditional.size = 1;
+    cudaGraphNode_t node;
+    e = cudaGraphAddNode(&node, lg.graph, nullptr, nullptr, 0, &p);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(lg.graph);
+        return cuda_fail(e, "cudaGraphAddNode(conditional)", __FILE__, __LINE__);
+    }
+    cudaGraph_t body = p.conditional.phGraph_out[0];
+    e = cudaStreamBeginCaptureToGraph(g->cap, body, nullptr, nullptr, 0,
+                                      cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        cudaError_t ek = (g->id_bits == 64)
+                             ? enqueue_block<int64_t>(g, order, mode, c, (int64_t*)L, (int64_t*)Lu, loop, g->cap)
+                             : enqueue_block<int32_t>(g, order, mode, c, (int32_t*)L, (int32_t*)Lu, loop, g->cap);
+        cudaGraph_t captured = nullptr;
+        e = cudaStreamEndCapture(g->cap, &captured);
+        if (ek != cudaSuccess) e = ek;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&lg.exec, lg.graph, 0);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(lg.graph);
+        return cuda_fail(e, "building the sweep loop graph", __FILE__, __LINE__);
+    }
+    *out = lg;
+    return CC_OK;
+}
+
+static cc_status get_loop(cc_graph* g, int order, int mode, int c, void* L, void* Lu,
+                          cudaGraphExec_t* exec) {
+    for (auto& lg : g->loops)
+        if (lg.order == order && lg.mode == mode && lg.c == c && lg.L == L && lg.Lu == Lu) {
+            *exec = lg.exec;
+            return CC_OK;
+        }
+    // keep a few: a loop graph bakes in the label buffer of the run
+    if (g->loops.size() >= 8) {
+        cudaGraphExecDestroy(g->loops.front().exec);
+        cudaGraphDestroy(g->loops.front().graph);
+        g->loops.erase(g->loops.begin());
+    }
+    LoopGraph lg;
+    cc_status st = build_loop(g, order, mode, c, L, Lu, &lg);
+    if (st != CC_OK) return st;
+    g->loops.push_back(lg);
+    *exec = lg.exec;
+    return CC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// cc_init
+// ---------------------------------------------------------------------------
+
+template <typename IdT>
+static cc_status init_edges(cc_graph* g, int layout, const void* a, const void* b, int64_t cnt,
+                            int on_device, cudaStream_t s) {
+    const size_t B = sizeof(IdT);
+    const int64_t n = g->n;
+    g->m = cnt;
+    const bool aligned = on_device && ((reinterpret_cast<uintptr_t>(a) | reinterpret_cast<uintptr_t>(b)) & 15) == 0;
+    if (layout == CC_COO && aligned) {
+        g->src = const_cast<void*>(a);
+        g->dst = const_cast<void*>(b);
+        g->own_edges = false;
+    } else {
+        g->own_edges = true;
+        const size_t bytes = (size_t)(cnt > 0 ? cnt : 1) * B;
+        CC_CUDA(cudaMalloc(&g->src, bytes));
+        CC_CUDA(cudaMalloc(&g->dst, bytes));
+        const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+        if (layout == CC_COO) {
+            if (cnt) {
+                CC_CUDA(cudaMemcpyAsync(g->src, a, cnt * B, kind, s));
+                CC_CUDA(cudaMemcpyAsync(g->dst, b, cnt * B, kind, s));
+            }
+        } else {
+            // CSR: offsets (int64, n+1) and columns; rows are expanded on the device
+            int64_t* off = nullptr;
+            CC_CUDA(cudaMalloc(&off, (size_t)(n + 1) * sizeof(int64_t)));
+            cudaError_t e = cudaMemcpyAsync(off, a, (size_t)(n + 1) * sizeof(int64_t), kind, s);
+            if (e == cudaSuccess && cnt) e = cudaMemcpyAsync(g->dst, b, cnt * B, kind, s);
+            if (e == cudaSuccess) {
+                auto kv = cc::validate_offsets_kernel;
+                kv<<<grid_for(kv, n + 1), kThreads, 0, s>>>(off, n, cnt, g->ctl);
+                e = cudaGetLastError();
+            }
+            if (e == cudaSuccess) {
+                CC_CUDA(cudaMemcpyAsync(g->ctl_h, g->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
+                e = cudaStreamSynchronize(s);
+            }
+            if (e == cudaSuccess && g->ctl_h->bad_count) {
+                cudaFree(off);
+                return set_error(CC_EINVAL, "CSR offsets are not non-decreasing from 0 to nnz=%lld (first bad index %llu)",
+                                 (long long)cnt, g->ctl_h->first_bad);
+            }
+            if (e == cudaSuccess && cnt) {
+                auto kr = cc::csr_rows_kernel<IdT>;
+                kr<<<grid_for(kr, cnt), kThreads, 0, s>>>(off, n, cnt, static_cast<IdT*>(g->src));
+                e = cudaGetLastError();
+            }
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+            cudaFree(off);
+            if (e != cudaSuccess) return cuda_fail(e, "CSR expansion", __FILE__, __LINE__);
+        }
+    }
+    // every endpoint must lie in [0, n)
+    if (cnt) {
+        auto kv = cc::validate_ids_kernel<IdT>;
+        const int grid = grid_for(kv, cnt);
+        kv<<<grid, kThreads, 0, s>>>(static_cast<const IdT*>(g->src), cnt, n, g->ctl);
+        CC_LAUNCHED();
+        kv<<<grid, kThreads, 0, s>>>(static_cast<const IdT*>(g->dst), cnt, n, g->ctl);
+        CC_LAUNCHED();
+    }
+    CC_CUDA(cudaMemcpyAsync(g->ctl_h, g->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
+    CC_CUDA(cudaStreamSynchronize(s));
+    if (g->ctl_h->bad_count)
+        return set_error(CC_EIDRANGE, "%llu edge endpoints outside [0, %lld) (first at entry %llu of src or dst)",
+                         g->ctl_h->bad_count, (long long)n, g->ctl_h->first_bad);
+    return CC_OK;
+}
+
+extern "C" cc_status cc_init(cc_graph** out, int64_t n, int id_bits, int layout, const void* a,
+                             const void* b, int64_t cnt, int on_device, void* cuda_stream) {
+    g_last_error.clear();
+    if (!out) return set_error(CC_EINVAL, "cc_init: g is NULL");
+    *out = nullptr;
+    if (n < 0 || cnt < 0) return set_error(CC_EINVAL, "cc_init: negative n or m");
+    if (id_bits != CC_ID32 && id_bits != CC_ID64) return set_error(CC_EINVAL, "cc_init: id_bits must be 32 or 64");
+    if (id_bits == CC_ID32 && n > 0x7fffffffLL) return set_error(CC_EINVAL, "cc_init: n >= 2^31 needs CC_ID64");
+    if (layout != CC_COO && layout != CC_CSR) return set_error(CC_EINVAL, "cc_init: bad layout");
+    if (layout == CC_CSR && !a) return set_error(CC_EINVAL, "cc_init: CSR offsets are NULL");
+    if (cnt > 0 && (!a || !b)) return set_error(CC_EINVAL, "cc_init: edge arrays are NULL");
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+
+    cc_graph* g = new (std::nothrow) cc_graph();
+    if (!g) return set_error(CC_ENOMEM, "cc_init: host allocation failed");
+    g->n = n;
+    g->id_bits = id_bits;
+    g->stream = s;
+    cc_status st = CC_OK;
+    auto fail = [&](cc_status x) {
+        destroy(g);
+        return x;
+    };
+    {
+        cudaError_t e = cudaMalloc(&g->ctl, sizeof(Ctl));
+        if (e == cudaSuccess) e = cudaMallocHost(&g->ctl_h, sizeof(Ctl));
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&g->cap, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreate(&g->ev0);
+        if (e == cudaSuccess) e = cudaEventCreate(&g->ev1);
+        if (e == cudaSuccess) e = cudaEventCreate(&g->evl0);
+        if (e == cudaSuccess) e = cudaEventCreate(&g->evl1);
+        if (e != cudaSuccess) return fail(cuda_fail(e, "cc_init allocation", __FILE__, __LINE__));
+    }
+    cc::ctl_reset_kernel<<<1, 32, 0, s>>>(g->ctl, 1);
+    if (cudaGetLastError() != cudaSuccess) return fail(set_error(CC_ECUDA, "cc_init: launch failed"));
+    st = (id_bits == 64) ? init_edges<int64_t>(g, layout, a, b, cnt, on_device, s)
+                         : init_edges<int32_t>(g, layout, a, b, cnt, on_device, s);
+    if (st != CC_OK) return fail(st);
+    *out = g;
+    return CC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// cc_run
+// ---------------------------------------------------------------------------
+
+template <typename IdT>
+static cudaError_t enqueue_init(cc_graph* g, IdT* L, IdT* Lu, const void* init, cudaStream_t s) {
+    if (init) {
+        if ((void*)L != init) {
+            cudaError_t e = cudaMemcpyAsync(L, init, g->n * sizeof(IdT), cudaMemcpyDefault, s);
+            if (e != cudaSuccess) return e;
+        }
+        auto kv = cc::validate_snapshot_kernel<IdT>;
+        kv<<<grid_for(kv, g->n), kThreads, 0, s>>>(L, g->n, g->ctl);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        if (Lu) return launch_copy<IdT>(Lu, L, g->n, s);
+        return cudaSuccess;
+    }
+    auto k = cc::iota_kernel<IdT>;
+    k<<<grid_for(k, g->n), kThreads, 0, s>>>(L, Lu, g->n);
+    return cudaGetLastError();
+}
+
+template <typename IdT>
+static cudaError_t enqueue_compress(cc_graph* g, IdT* L, cudaStream_t s) {
+    auto k = cc::compress_kernel<IdT>;
+    k<<<grid_for(k, g->n), kThreads, 0, s>>>(L, g->n, g->ctl);
+    return cudaGetLastError();
+}
+
+extern "C" cc_status cc_run_impl(cc_graph* g, int order, int mode, int c, int32_t max_sweeps,
+                                 const void* init_labels, void* labels_out, int out_on_device,
+                                 cc_stats* stats, cudaStream_t s);
+
+extern "C" cc_status cc_run(cc_graph* g, int order, int mode, int c, int32_t max_sweeps,
+                            const void* init_labels, void* labels_out, int out_on_device,
+                            cc_stats* stats) {
+    return cc_run_impl(g, order, mode, c, max_sweeps, init_labels, labels_out, out_on_device, stats,
+                       g ? g->stream : nullptr);
+}
+
+extern "C" cc_status cc_graph_set_stream(cc_graph* g, void* cuda_stream) {
+    if (!g) return set_error(CC_EINVAL, "cc_graph_set_stream: g is NULL");
+    g->stream = static_cast<cudaStream_t>(cuda_stream);
+    return CC_OK;
+}
+
+extern "C" cc_status cc_run_impl(cc_graph* g, int order, int mode, int c, int32_t max_sweeps,
+                                 const void* init_labels, void* labels_out, int out_on_device,
+                                 cc_stats* stats, cudaStream_t s) {
+    g_last_error.clear();
+    if (!g) return set_error(CC_EINVAL, "cc_run: g is NULL");
+    if (g->n > 0 && !labels_out) return set_error(CC_EINVAL, "cc_run: labels_out is NULL");
+    if (order == CC_ORDER_AUTO) {
+        cc_status st = cc::resolve_schedule(g, &order, &mode, &c);
+        if (st != CC_OK) return st;
+    }
+    if (order < 0 || order > CC_MAX_ORDER) return set_error(CC_EINVAL, "cc_run: order must be 1..%d, CC_ORDER_FULL or CC_ORDER_AUTO", CC_MAX_ORDER);
+    if (mode != CC_SYNC && mode != CC_ASYNC) return set_error(CC_EINVAL, "cc_run: mode must be CC_SYNC or CC_ASYNC");
+    if (c < 1 || c > 64) return set_error(CC_EINVAL, "cc_run: check_interval must be 1..64");
+    if (max_sweeps < 1) return set_error(CC_EINVAL, "cc_run: max_sweeps must be >= 1");
+    const size_t B = id_size(g->id_bits);
+    if (stats) {
+        std::memset(stats, 0, sizeof *stats);
+        stats->order = order;
+        stats->mode = mode;
+        stats->check_interval = c;
+    }
+    if (g->n == 0) return CC_OK;
+
+    void* L = labels_out;
+    if (!out_on_device || (reinterpret_cast<uintptr_t>(labels_out) & 15)) {
+        if (!g->L) CC_CUDA(cudaMalloc(&g->L, g->n * B));
+        L = g->L;
+    }
+    void* Lu = nullptr;
+    if (mode == CC_SYNC) {
+        if (!g->Lu) CC_CUDA(cudaMalloc(&g->Lu, g->n * B));
+        Lu = g->Lu;
+    }
+    cudaGraphExec_t loop = nullptr;
+    {
+        cc_status st = get_loop(g, order, mode, c, L, Lu, &loop);
+        if (st != CC_OK) return st;
+    }
+
+    CC_CUDA(cudaEventRecord(g->ev0, s));
+    cc::ctl_reset_kernel<<<1, 32, 0, s>>>(g->ctl, max_sweeps);
+    CC_LAUNCHED();
+    CC_CUDA(g->id_bits == 64 ? enqueue_init<int64_t>(g, (int64_t*)L, (int64_t*)Lu, init_labels, s)
+                             : enqueue_init<int32_t>(g, (int32_t*)L, (int32_t*)Lu, init_labels, s));
+    if (init_labels) {
+        // a bad snapshot could point outside [0, n): check before any gather
+        CC_CUDA(cudaMemcpyAsync(g->ctl_h, g->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
+        CC_CUDA(cudaStreamSynchronize(s));
+        if (g->ctl_h->bad_count)
+            return set_error(CC_EINVAL, "cc_run: init_labels violates 0 <= L[x] <= x at %llu entries (first %llu)",
+                             g->ctl_h->bad_count, g->ctl_h->first_bad);
+    }
+    CC_CUDA(cudaEventRecord(g->evl0, s));
+    CC_CUDA(cudaGraphLaunch(loop, s));
+    CC_CUDA(cudaEventRecord(g->evl1, s));
+    CC_CUDA(g->id_bits == 64 ? enqueue_compress<int64_t>(g, (int64_t*)L, s)
+                             : enqueue_compress<int32_t>(g, (int32_t*)L, s));
+    CC_CUDA(cudaEventRecord(g->ev1, s));
+    if (L != labels_out)
+        CC_CUDA(cudaMemcpyAsync(labels_out, L, g->n * B, cudaMemcpyDefault, s));
+    CC_CUDA(cudaMemcpyAsync(g->ctl_h, g->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
+    CC_CUDA(cudaStreamSynchronize(s));
+
+    const Ctl& h = *g->ctl_h;
+    if (stats) {
+        float ms = 0.f, lms = 0.f;
+        cudaEventElapsedTime(&ms, g->ev0, g->ev1);
+        cudaEventElapsedTime(&lms, g->evl0, g->evl1);
+        stats->sweeps = h.sweeps;
+        stats->solve_ms = ms;
+        stats->loop_ms = lms;
+        stats->edges_per_s = ms > 0 ? (double)g->m / (ms * 1e-3) : 0.0;
+        double per = 2.0 * B * (double)g->m + B * (double)g->n;
+        if (mode == CC_SYNC) per += 3.0 * B * (double)g->n;
+        stats->alg_bytes = per * h.sweeps;
+    }
+    if (!h.converged)
+        return set_error(CC_ENOTCONVERGED, "cc_run: not converged after %d sweeps", h.sweeps);
+    if (h.compress_changes)
+        return set_error(CC_ECUDA, "cc_run: converged state was not a set of stars (%llu labels moved)",
+                         h.compress_changes);
+    return CC_OK;
+}
+
+extern "C" cc_status cc_graph_info(const cc_graph* g, int64_t* n, int64_t* m) {
+    if (!g) return set_error(CC_EINVAL, "cc_graph_info: g is NULL");
+    if (n) *n = g->n;
+    if (m) *m = g->m;
+    return CC_OK;
+}
+
+extern "C" void cc_free(cc_graph* g) { destroy(g); }
+
+extern "C" const char* cc_strerror(cc_status s) {
+    switch (s) {
+        case CC_OK: return "success";
+        case CC_EINVAL: return "invalid argument";
+        case CC_EIDRANGE: return "vertex id out of range";
+        case CC_ENOMEM: return "out of memory";
+        case CC_ECUDA: return "CUDA error";
+        case CC_ENOTCONVERGED: return "not converged within max_sweeps";
+        case CC_ETIMEOUT: return "device-side wait timed out";
+    }
+    return "unknown status";
+}
+
+extern "C" const char* cc_last_error(void) { return g_last_error.c_str(); }
+
+// Internals shared with the other translation units.
+namespace cc {
+const void* graph_src(const cc_graph* g) { return g->src; }
+const void* graph_dst(const cc_graph* g) { return g->dst; }
+int graph_id_bits(const cc_graph* g) { return g->id_bits; }
+cc_status graph_nm(const cc_graph* g, long long* n, long long* m) {
+    *n = g->n;
+    *m = g->m;
+    return CC_OK;
+}
+}  // namespace cc

@@ -1,0 +1,341 @@
+// Device kernels of the single-graph Contour path (sm_103a).
+//
+// Every kernel here works on a label array L[0..n-1] of vertex ids (int32_t or
+// int64_t) and on an edge list given as two id arrays src[m], dst[m].
+//
+// Invariant relied on for memory safety: every value ever stored in L lies in
+// [0, n) and satisfies L[x] <= x.  Labels start as ids (Alg. 1) or as a
+// validated snapshot, and every store writes a value that was read from L, so
+// every gather L[y] below is in bounds and every label chain strictly
+// decreases until it reaches a root (L[r] == r).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace cc {
+
+// Device-side control block of one graph handle.
+struct Ctl {
+    int32_t flag;        // 1 if the checked sweep saw an edge that lowers a label
+    int32_t sweeps;      // sweeps executed so far
+    int32_t max_sweeps;  // stop after this many sweeps
+    int32_t converged;   // 1 once a checked sweep saw no such edge
+    unsigned long long bad_count;         // validation failures
+    unsigned long long first_bad;         // smallest failing index
+    unsigned long long compress_changes;  // labels changed by the final compress
+    unsigned long long pad;
+};
+
+constexpr int kFullChainHops = 1024;  // cap of the full-chain operator ("C-m", m = 1024)
+
+// ---------------------------------------------------------------------------
+// memory access helpers
+// ---------------------------------------------------------------------------
+
+// Edge stream: read once per sweep, never reused -> evict-first at L1 and L2.
+__device__ __forceinline__ void load4(const int32_t* p, int32_t (&o)[4]) {
+    int4 v = __ldcs(reinterpret_cast<const int4*>(p));
+    o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+}
+__device__ __forceinline__ void load4(const int64_t* p, int64_t (&o)[4]) {
+    longlong2 a = __ldcs(reinterpret_cast<const longlong2*>(p));
+    longlong2 b = __ldcs(reinterpret_cast<const longlong2*>(p) + 1);
+    o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y;
+}
+
+// Label gather.  Synchronous sweeps never write L, so its reads may use the
+// read-only path; asynchronous sweeps read L while other threads store into it.
+template <bool SYNC, typename IdT>
+__device__ __forceinline__ IdT rd(const IdT* L, IdT x) {
+    if constexpr (SYNC) return __ldg(L + x);
+    else return L[x];
+}
+
+// Conditional assignment x <- z (Def. 1).  The caller has already seen the
+// old value exceed z.  Synchronous: atomic minimum into L_u (the CAS loop of
+// Eq. "cas" collapses to one reduction); asynchronous: a plain store into L
+// (Section III-B3: a lost write costs iterations, never correctness).
+template <bool SYNC, typename IdT>
+__device__ __forceinline__ void wr(IdT* L, IdT* Lu, IdT x, IdT z) {
+    if constexpr (SYNC) {
+        if constexpr (sizeof(IdT) == 4) atomicMin(reinterpret_cast<int*>(Lu) + x, (int)z);
+        else atomicMin(reinterpret_cast<long long*>(Lu) + x, (long long)z);
+    } else {
+        L[x] = z;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// MM^h on K edges held in registers (h = H fixed at compile time)
+// ---------------------------------------------------------------------------
+//
+// For edge <w, v>: chain c[0] = w, c[j] = L[c[j-1]] (j = 1..H);
+// z = min(cw[H], cv[H]); every chain vertex c[j], j < H, whose label c[j+1]
+// exceeds z is set to z (Def. 3).  Chains never increase (L[x] <= x), so some
+// write is due exactly when max(L[w], L[v]) > z; for H = 2 that is the
+// early-convergence test of Section III-B2 (L[v] != L^2[v] || L[w] != L^2[w]
+// || L[v] != L[w]).  All loads of the K edges are issued before any store so
+// that their latencies overlap.
+template <int H, bool SYNC, int K, typename IdT>
+__device__ __forceinline__ bool mm_fixed(const IdT (&w)[K], const IdT (&v)[K], IdT* L, IdT* Lu) {
+    IdT cw[K][H + 1], cv[K][H + 1];
+#pragma unroll
+    for (int k = 0; k < K; ++k) { cw[k][0] = w[k]; cv[k][0] = v[k]; }
+#pragma unroll
+    for (int j = 1; j <= H; ++j) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            cw[k][j] = rd<SYNC>(L, cw[k][j - 1]);
+            cv[k][j] = rd<SYNC>(L, cv[k][j - 1]);
+        }
+    }
+    bool viol = false;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const IdT z = cw[k][H] < cv[k][H] ? cw[k][H] : cv[k][H];
+        viol |= (cw[k][1] > z) | (cv[k][1] > z);
+#pragma unroll
+        for (int j = 0; j < H; ++j) {
+            if (cw[k][j + 1] > z) wr<SYNC>(L, Lu, cw[k][j], z);
+            if (cv[k][j + 1] > z) wr<SYNC>(L, Lu, cv[k][j], z);
+        }
+    }
+    return viol;
+}
+
+// ---------------------------------------------------------------------------
+// MM^h with h chosen at run time (orders other than 1, 2, 4, and the full
+// chain).  The chain is walked twice: once to find z, once to write.  A walk
+// stops early at a root (L[r] == r), where the chain would only repeat r.
+// ---------------------------------------------------------------------------
+template <bool SYNC, typename IdT>
+__device__ __forceinline__ void rewalk(IdT x, IdT z, int h, IdT* L, IdT* Lu) {
+    for (int j = 0; j < h; ++j) {
+        const IdT y = rd<SYNC>(L, x);
+        if (y <= z) break;  // labels further down the chain are <= y
+        wr<SYNC>(L, Lu, x, z);
+        if (y == x) break;  // root
+        x = y;
+    }
+}
+
+template <bool SYNC, typename IdT>
+__device__ __forceinline__ bool mm_runtime(IdT w, IdT v, int h, IdT* L, IdT* Lu) {
+    IdT ew = w, ev = v, fw = w, fv = v;
+    bool dw = false, dv = false;
+    for (int j = 0; j < h && !(dw && dv); ++j) {
+        if (!dw) {
+            const IdT y = rd<SYNC>(L, ew);
+            if (j == 0) fw = y;
+            dw = (y == ew);
+            ew = y;
+        }
+        if (!dv) {
+            const IdT y = rd<SYNC>(L, ev);
+            if (j == 0) fv = y;
+            dv = (y == ev);
+            ev = y;
+        }
+    }
+    const IdT z = ew < ev ? ew : ev;
+    const bool viol = (fw > z) | (fv > z);
+    if (fw > z) rewalk<SYNC>(w, z, h, L, Lu);
+    if (fv > z) rewalk<SYNC>(v, z, h, L, Lu);
+    return viol;
+}
+
+// ---------------------------------------------------------------------------
+// the sweep: every edge once (Alg. 1 edge loop)
+// ---------------------------------------------------------------------------
+//
+// Grid-stride over groups of 4 edges loaded with 16-byte streaming loads
+// (src and dst are 16-byte aligned); the m % 4 tail edges are taken by the
+// first threads of the grid.  H = 0 selects the run-time order h.
+// flag == nullptr: sweep without convergence check (inside a check block).
+template <int H, bool SYNC, int G, typename IdT>
+__global__ void __launch_bounds__(256)
+mm_sweep_kernel(const IdT* __restrict__ src, const IdT* __restrict__ dst, int64_t m,
+                IdT* L, IdT* Lu, int h, int32_t* flag) {
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t ngroups = m / (4 * G);
+    bool viol = false;
+    for (int64_t g = tid; g < ngroups; g += stride) {
+        IdT w[4 * G], v[4 * G];
+#pragma unroll
+        for (int q = 0; q < G; ++q) {
+            IdT t[4];
+            load4(src + (g * G + q) * 4, t);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) w[4 * q + i] = t[i];
+            load4(dst + (g * G + q) * 4, t);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) v[4 * q + i] = t[i];
+        }
+        if constexpr (H > 0) {
+            viol |= mm_fixed<H, SYNC, 4 * G>(w, v, L, Lu);
+        } else {
+#pragma unroll 1
+            for (int k = 0; k < 4 * G; ++k) viol |= mm_runtime<SYNC>(w[k], v[k], h, L, Lu);
+        }
+    }
+    const int64_t tail0 = ngroups * 4 * G;
+    if (tid < m - tail0) {
+        IdT w[1] = {__ldcs(src + tail0 + tid)};
+        IdT v[1] = {__ldcs(dst + tail0 + tid)};
+        if constexpr (H > 0) viol |= mm_fixed<H, SYNC, 1>(w, v, L, Lu);
+        else viol |= mm_runtime<SYNC>(w[0], v[0], h, L, Lu);
+    }
+    if (flag != nullptr) {
+        // one store per block, only when some edge of the block could lower a label
+        if (__syncthreads_or(viol) && threadIdx.x == 0) *flag = 1;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// label initialisation, copy, compress, validation
+// ---------------------------------------------------------------------------
+
+// L[i] = i and, for synchronous runs, L_u[i] = i (Alg. 1 initialisation).
+template <typename IdT>
+__global__ void iota_kernel(IdT* L, IdT* Lu, int64_t n) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        L[i] = (IdT)i;
+        if (Lu) Lu[i] = (IdT)i;
+    }
+}
+
+// dst[i] = src[i] for i < count ids, 16-byte vectors plus a scalar tail
+// (L = L_u of Alg. 1; both arrays are 256-byte aligned device allocations or
+// the caller's 16-byte aligned output).
+template <typename IdT>
+__global__ void copy_kernel(IdT* __restrict__ dst, const IdT* __restrict__ src, int64_t count) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    constexpr int per = 16 / sizeof(IdT);
+    const int64_t nv = count / per;
+    const int4* s4 = reinterpret_cast<const int4*>(src);
+    int4* d4 = reinterpret_cast<int4*>(dst);
+    for (int64_t i = tid; i < nv; i += stride) d4[i] = s4[i];
+    const int64_t t = nv * per + tid;
+    if (t < count) dst[t] = src[t];
+}
+
+// Final compress: L[x] becomes the root of x's chain, so the pointer graph is
+// a set of stars (Section II-A).  At a fixed point of the sweep this changes
+// nothing; the number of changed labels is reported for checking.  Chains
+// strictly decrease, so each walk ends; the walk is still capped.
+// Runs only after a converged loop; a partial state (max_sweeps reached) is
+// left exactly as the last sweep wrote it, so that it resumes bit-exactly.
+template <typename IdT>
+__global__ void compress_kernel(IdT* L, int64_t n, Ctl* ctl) {
+    if (!ctl->converged) return;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    unsigned long long changes = 0;
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += stride) {
+        const IdT l = L[x];
+        IdT r = l;
+        IdT p = L[r];
+        for (int guard = 0; p != r && guard < (1 << 24); ++guard) {
+            r = p;
+            p = L[r];
+        }
+        if (r != l) {
+            L[x] = r;
+            ++changes;
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) changes += __shfl_xor_sync(0xffffffffu, changes, o);
+    if ((threadIdx.x & 31) == 0 && changes) atomicAdd(&ctl->compress_changes, changes);
+}
+
+// Count ids outside [0, n) and record the smallest failing index.
+template <typename IdT>
+__global__ void validate_ids_kernel(const IdT* ids, int64_t count, int64_t n, Ctl* ctl) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    unsigned long long bad = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += stride) {
+        const IdT x = ids[i];
+        if (x < 0 || (int64_t)x >= n) {
+            ++bad;
+            atomicMin(&ctl->first_bad, (unsigned long long)i);
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) bad += __shfl_xor_sync(0xffffffffu, bad, o);
+    if ((threadIdx.x & 31) == 0 && bad) atomicAdd(&ctl->bad_count, bad);
+}
+
+// A resume snapshot must satisfy 0 <= L[x] <= x (labels never exceed ids).
+template <typename IdT>
+__global__ void validate_snapshot_kernel(const IdT* L, int64_t n, Ctl* ctl) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    unsigned long long bad = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const IdT x = L[i];
+        if (x < 0 || (int64_t)x > i) {
+            ++bad;
+            atomicMin(&ctl->first_bad, (unsigned long long)i);
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) bad += __shfl_xor_sync(0xffffffffu, bad, o);
+    if ((threadIdx.x & 31) == 0 && bad) atomicAdd(&ctl->bad_count, bad);
+}
+
+// CSR offsets must run from 0 to nnz without decreasing.
+__global__ void validate_offsets_kernel(const int64_t* off, int64_t n, int64_t nnz, Ctl* ctl) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    unsigned long long bad = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i <= n; i += stride) {
+        const int64_t o = off[i];
+        bool ok = (i == 0) ? (o == 0) : (o >= off[i - 1]);
+        if (i == n) ok = ok && (o == nnz);
+        if (!ok) {
+            ++bad;
+            atomicMin(&ctl->first_bad, (unsigned long long)i);
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) bad += __shfl_xor_sync(0xffffffffu, bad, o);
+    if ((threadIdx.x & 31) == 0 && bad) atomicAdd(&ctl->bad_count, bad);
+}
+
+// CSR -> COO: entry k belongs to the row r with off[r] <= k < off[r+1].
+template <typename IdT>
+__global__ void csr_rows_kernel(const int64_t* off, int64_t n, int64_t nnz, IdT* rows) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nnz; k += stride) {
+        int64_t lo = 0, hi = n;  // largest r with off[r] <= k
+        while (hi - lo > 1) {
+            const int64_t mid = (lo + hi) >> 1;
+            if (off[mid] <= k) lo = mid; else hi = mid;
+        }
+        rows[k] = (IdT)lo;
+    }
+}
+
+__global__ void ctl_reset_kernel(Ctl* ctl, int32_t max_sweeps) {
+    if (threadIdx.x == 0) {
+        ctl->flag = 0;
+        ctl->sweeps = 0;
+        ctl->max_sweeps = max_sweeps;
+        ctl->converged = 0;
+        ctl->bad_count = 0;
+        ctl->first_bad = ~0ull;
+        ctl->compress_changes = 0;
+    }
+}
+
+// End of one check block inside the conditional WHILE body: read and clear the
+// flag, count the block's sweeps, and decide whether the loop runs again.
+__global__ void check_kernel(Ctl* ctl, int32_t block_sweeps, cudaGraphConditionalHandle loop) {
+    if (threadIdx.x == 0) {
+        const int32_t f = ctl->flag;
+        ctl->flag = 0;
+        ctl->sweeps += block_sweeps;
+        ctl->converged = (f == 0);
+        cudaGraphSetConditional(loop, (f != 0 && ctl->sweeps < ctl->max_sweeps) ? 1u : 0u);
+    }
+}
+
+}  // namespace cc

@@ -1,0 +1,59 @@
+"""The C ABI library loads and exports every function include/*.h declares (no GPU)."""
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", "", text)
+        for mt in re.finditer(r"\b(cc_[A-Za-z0-9_]+)\s*\(", text):
+            names.add(mt.group(1))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def built_lib():
+    import __graft_entry__
+    path = __graft_entry__._builder().build()
+    return ctypes.CDLL(path)
+
+
+def test_header_declares_the_entry_points():
+    names = _declared()
+    for want in ("cc_init", "cc_run", "cc_free", "cc_strerror"):
+        assert want in names
+
+
+def test_library_exports_every_declared_symbol(built_lib):
+    missing = [n for n in _declared() if not hasattr(built_lib, n)]
+    assert not missing, missing
+
+
+def test_strerror_without_gpu(built_lib):
+    import paper_2311_02811_gb300 as cc
+    assert cc.cc_strerror(cc.CC_OK) == "success"
+    assert cc.cc_strerror(cc.CC_EIDRANGE) == "vertex id out of range"
+    assert cc.cc_strerror(99) == "unknown status"
+
+
+def test_argument_errors_need_no_gpu(built_lib):
+    """Host-side argument checks run before any CUDA call."""
+    import paper_2311_02811_gb300 as cc
+    g = ctypes.c_void_p()
+    assert cc.lib.cc_init(None, 4, 32, 0, None, None, 0, 0, None) == cc.CC_EINVAL
+    assert cc.lib.cc_init(ctypes.byref(g), -1, 32, 0, None, None, 0, 0, None) == cc.CC_EINVAL
+    assert cc.lib.cc_init(ctypes.byref(g), 4, 16, 0, None, None, 0, 0, None) == cc.CC_EINVAL
+    assert cc.lib.cc_init(ctypes.byref(g), 1 << 31, 32, 0, None, None, 0, 0, None) == cc.CC_EINVAL
+    assert cc.lib.cc_init(ctypes.byref(g), 4, 32, 7, None, None, 0, 0, None) == cc.CC_EINVAL
+    assert cc.lib.cc_init(ctypes.byref(g), 4, 32, 0, None, None, 3, 0, None) == cc.CC_EINVAL
+    assert "NULL" in cc.cc_last_error()
+    assert cc.lib.cc_run(None, 2, 1, 1, 10, None, None, 0, None) == cc.CC_EINVAL
