@@ -139,6 +139,43 @@ cc_status cc_init(cc_graph **g, int64_t n, int id_bits, int layout, const void *
 cc_status cc_run(cc_graph *g, int order, int mode, int check_interval, int32_t max_sweeps,
                  const void *init_labels, void *labels_out, int out_on_device, cc_stats *stats);
 
+/*
+ * cc_run_noalloc -- the same computation as cc_run, for callers that cannot
+ * allocate device memory.  The paper has no counterpart to this entry point.
+ *
+ * Who needs it: code whose device memory belongs to someone else -- a plugin
+ * or serving loop inside a framework that owns a pre-reserved memory pool and
+ * forbids cudaMalloc during a step, or a latency-critical loop that cannot
+ * afford cudaMalloc/cudaFree, which may synchronise the whole device.  Such a
+ * caller passes only its own inputs and outputs; no handle is created.
+ *
+ * Memory: the control words and, for CC_SYNC, the update array L_u live in
+ * one fixed device array inside libcontour.so (4 * CC_NOALLOC_MAX_N bytes plus
+ * 256), held by every GPU that loads it until the process exits.  No call to
+ * cudaMalloc, cudaFree, graph instantiation or any other allocating routine is
+ * made; the convergence flag is read back by the host after every check block.
+ *
+ *   n, src, dst, m  int32 COO edges on the device (ids in [0, n), checked:
+ *                   CC_EIDRANGE); src, dst and labels_out must be 16-byte
+ *                   aligned (CC_EINVAL otherwise) and are never copied.
+ *   order, mode, check_interval, max_sweeps  as for cc_run (no CC_ORDER_AUTO).
+ *   labels_out      n int32 device labels; also the working label array.
+ *   sweeps_out      NULL or the number of sweeps executed.
+ *   cuda_stream     stream to run on; synchronised before returning.
+ *
+ * Limits: CC_SYNC requires n <= CC_NOALLOC_MAX_N (CC_EINVAL beyond it, before
+ * any device work); CC_ASYNC needs no L_u and accepts any n < 2^31.
+ * The first call on each device looks up the array's device address (with
+ * that device current), so make that first call before any stream capture.
+ * Every call in the process shares the one array and clears the words it
+ * needs at the start: calls that may overlap on the GPU (different streams or
+ * threads) race and must be serialised by the caller.
+ */
+enum { CC_NOALLOC_MAX_N = 4194304 };
+cc_status cc_run_noalloc(int64_t n, const int32_t *src, const int32_t *dst, int64_t m, int order,
+                         int mode, int check_interval, int32_t max_sweeps, int32_t *labels_out,
+                         int32_t *sweeps_out, void *cuda_stream);
+
 /* Make later cc_run calls on g enqueue on another stream (default: the stream
  * passed to cc_init). */
 cc_status cc_graph_set_stream(cc_graph *g, void *cuda_stream);

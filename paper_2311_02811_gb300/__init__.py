@@ -17,8 +17,8 @@ import os
 __all__ = [
     "CC_OK", "CC_EINVAL", "CC_EIDRANGE", "CC_ENOMEM", "CC_ECUDA", "CC_ENOTCONVERGED",
     "CC_ETIMEOUT", "CC_ID32", "CC_ID64", "CC_COO", "CC_CSR", "CC_SYNC", "CC_ASYNC",
-    "CC_ORDER_FULL", "CC_ORDER_AUTO", "CCError", "cc_stats", "cc_graph", "lib", "LIB_PATH",
-    "cc_init", "cc_run", "cc_free", "cc_graph_info", "cc_graph_set_stream", "cc_strerror",
+    "CC_ORDER_FULL", "CC_ORDER_AUTO", "CC_NOALLOC_MAX_N", "CCError", "cc_stats", "cc_graph", "lib", "LIB_PATH",
+    "cc_init", "cc_run", "cc_run_noalloc", "cc_free", "cc_graph_info", "cc_graph_set_stream", "cc_strerror",
     "cc_last_error",
 ]
 
@@ -29,6 +29,7 @@ CC_ID32, CC_ID64 = 32, 64
 CC_COO, CC_CSR = 0, 1
 CC_SYNC, CC_ASYNC = 0, 1
 CC_ORDER_FULL, CC_ORDER_AUTO = 0, -1
+CC_NOALLOC_MAX_N = 4194304
 
 
 class cc_stats(ctypes.Structure):
@@ -60,6 +61,9 @@ lib.cc_init.argtypes = [ctypes.POINTER(_p), _i64, _int, _int, _p, _p, _i64, _int
 lib.cc_init.restype = _int
 lib.cc_run.argtypes = [_p, _int, _int, _int, _i32, _p, _p, _int, ctypes.POINTER(cc_stats)]
 lib.cc_run.restype = _int
+lib.cc_run_noalloc.argtypes = [_i64, _p, _p, _i64, _int, _int, _int, _i32, _p,
+                               ctypes.POINTER(_i32), _p]
+lib.cc_run_noalloc.restype = _int
 lib.cc_graph_info.argtypes = [_p, ctypes.POINTER(_i64), ctypes.POINTER(_i64)]
 lib.cc_graph_info.restype = _int
 lib.cc_graph_set_stream.argtypes = [_p, _p]
@@ -163,6 +167,25 @@ def cc_run(g, labels_out, order=2, mode=CC_ASYNC, check_interval=1, max_sweeps=1
         _check(rc, "cc_run", st)
         return st
     return rc, st
+
+
+def cc_run_noalloc(n, src, dst, labels_out, order=2, mode=CC_ASYNC, check_interval=1,
+                   max_sweeps=1 << 20, stream=None, raise_on_error=True):
+    """cc_run without any device allocation (int32 device arrays); returns sweeps.
+
+    See cc_run_noalloc in contour.h: for callers that must not allocate device
+    memory; scratch comes from a fixed array inside the library."""
+    ps, _ = _ptr(src)
+    pd, _ = _ptr(dst)
+    po, _ = _ptr(labels_out)
+    sw = _i32(0)
+    rc = lib.cc_run_noalloc(int(n), ps, pd, len(src) if src is not None else 0, int(order),
+                            int(mode), int(check_interval), int(max_sweeps), po,
+                            ctypes.byref(sw), _stream(stream))
+    if raise_on_error:
+        _check(rc, "cc_run_noalloc")
+        return sw.value
+    return rc, sw.value
 
 
 def cc_graph_info(g):

@@ -425,14 +425,14 @@ static cudaError_t enqueue_compress(cc_graph* g, IdT* L, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-extern "C" cc_status cc_run_impl(cc_graph* g, int order, int mode, int c, int32_t max_sweeps,
-                                 const void* init_labels, void* labels_out, int out_on_device,
-                                 cc_stats* stats, cudaStream_t s);
+static cc_status run_impl(cc_graph* g, int order, int mode, int c, int32_t max_sweeps,
+                          const void* init_labels, void* labels_out, int out_on_device,
+                          cc_stats* stats, cudaStream_t s);
 
 extern "C" cc_status cc_run(cc_graph* g, int order, int mode, int c, int32_t max_sweeps,
                             const void* init_labels, void* labels_out, int out_on_device,
                             cc_stats* stats) {
-    return cc_run_impl(g, order, mode, c, max_sweeps, init_labels, labels_out, out_on_device, stats,
+    return run_impl(g, order, mode, c, max_sweeps, init_labels, labels_out, out_on_device, stats,
                        g ? g->stream : nullptr);
 }
 
@@ -442,9 +442,9 @@ extern "C" cc_status cc_graph_set_stream(cc_graph* g, void* cuda_stream) {
     return CC_OK;
 }
 
-extern "C" cc_status cc_run_impl(cc_graph* g, int order, int mode, int c, int32_t max_sweeps,
-                                 const void* init_labels, void* labels_out, int out_on_device,
-                                 cc_stats* stats, cudaStream_t s) {
+static cc_status run_impl(cc_graph* g, int order, int mode, int c, int32_t max_sweeps,
+                          const void* init_labels, void* labels_out, int out_on_device,
+                          cc_stats* stats, cudaStream_t s) {
     g_last_error.clear();
     if (!g) return set_error(CC_EINVAL, "cc_run: g is NULL");
     if (g->n > 0 && !labels_out) return set_error(CC_EINVAL, "cc_run: labels_out is NULL");

@@ -284,7 +284,7 @@ __global__ void validate_snapshot_kernel(const IdT* L, int64_t n, Ctl* ctl) {
 }
 
 // CSR offsets must run from 0 to nnz without decreasing.
-__global__ void validate_offsets_kernel(const int64_t* off, int64_t n, int64_t nnz, Ctl* ctl) {
+static __global__ void validate_offsets_kernel(const int64_t* off, int64_t n, int64_t nnz, Ctl* ctl) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     unsigned long long bad = 0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i <= n; i += stride) {
@@ -314,7 +314,7 @@ __global__ void csr_rows_kernel(const int64_t* off, int64_t n, int64_t nnz, IdT*
     }
 }
 
-__global__ void ctl_reset_kernel(Ctl* ctl, int32_t max_sweeps) {
+static __global__ void ctl_reset_kernel(Ctl* ctl, int32_t max_sweeps) {
     if (threadIdx.x == 0) {
         ctl->flag = 0;
         ctl->sweeps = 0;
@@ -328,7 +328,7 @@ __global__ void ctl_reset_kernel(Ctl* ctl, int32_t max_sweeps) {
 
 // End of one check block inside the conditional WHILE body: read and clear the
 // flag, count the block's sweeps, and decide whether the loop runs again.
-__global__ void check_kernel(Ctl* ctl, int32_t block_sweeps, cudaGraphConditionalHandle loop) {
+static __global__ void check_kernel(Ctl* ctl, int32_t block_sweeps, cudaGraphConditionalHandle loop) {
     if (threadIdx.x == 0) {
         const int32_t f = ctl->flag;
         ctl->flag = 0;
