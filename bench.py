@@ -38,7 +38,8 @@ def parse():
     p.add_argument("--steps", type=int, default=10)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    p.add_argument("--workload", default="rmat24", choices=["rmat24", "grid4096", "components64"])
+    p.add_argument("--workload", default="rmat24",
+                   help="rmat<scale> (default rmat24), grid4096 or components64")
     p.add_argument("--order", type=int, default=2)
     p.add_argument("--mode", choices=["async", "sync"], default="async")
     p.add_argument("--interval", type=int, default=1)
@@ -46,6 +47,9 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
+    p.add_argument("--entry", choices=["cc_run", "noalloc"], default="cc_run",
+                   help="cc_run (conditional CUDA-graph loop) or cc_run_noalloc (host-polled "
+                        "plain launches of the same sweep kernel; profilers can see each sweep)")
     return p.parse_args()
 
 
@@ -89,9 +93,11 @@ def max_over_ranks(x: float, world: int) -> float:
 # ---------------------------------------------------------------------------
 
 def make_workload(name: str, device, seed: int):
-    if name == "rmat24":
-        s, d = gg.rmat(24, seed=seed, device=device)
-        return (1 << 24), s, d, {"workload": "rmat-scale24", "graph": "R-MAT a/b/c/d=.57/.19/.19/.05, edge factor 16, ids permuted"}
+    if name.startswith("rmat"):
+        scale = int(name[4:])
+        s, d = gg.rmat(scale, seed=seed, device=device)
+        return (1 << scale), s, d, {"workload": f"rmat-scale{scale}",
+                                    "graph": "R-MAT a/b/c/d=.57/.19/.19/.05, edge factor 16, ids permuted"}
     if name == "grid4096":
         s, d = gg.grid(4096, 4096, seed=seed, device=device)
         return 4096 * 4096, s, d, {"workload": "grid-4096x4096", "graph": "4-neighbour grid, 5% edges deleted, ids permuted"}
@@ -233,13 +239,27 @@ def _peaks():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-def timed_runs(cc, g, out, n_steps, order, mode, interval, stream):
+class _NoallocStats:
+    def __init__(self, sweeps):
+        self.sweeps = sweeps
+        self.loop_ms = float("nan")
+
+
+def timed_runs(cc, g, out, n_steps, order, mode, interval, stream, edges=None):
+    """n_steps solves between two CUDA events on the launching stream.
+
+    ``edges`` = (n, src, dst) switches to cc_run_noalloc (plain launches)."""
     stats = []
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
     for _ in range(n_steps):
-        stats.append(cc.cc_run(g, out, order, mode, interval))
+        if edges is None:
+            stats.append(cc.cc_run(g, out, order, mode, interval))
+        else:
+            n, s, d = edges
+            stats.append(_NoallocStats(cc.cc_run_noalloc(n, s, d, out, order, mode, interval,
+                                                         stream=stream.cuda_stream)))
     ev1.record(stream)
     torch.cuda.synchronize()
     return ev0.elapsed_time(ev1), stats
@@ -252,20 +272,20 @@ def run_ours(args, rank, world, local):
     mode = cc.CC_ASYNC if args.mode == "async" else cc.CC_SYNC
     seed = gg.BASE_SEED + rank
     n, s, d, cfg = make_workload(args.workload, dev, seed)
+    torch.cuda.empty_cache()  # release the generator's temporaries
     m = s.numel()
     stream = torch.cuda.current_stream()
     g = cc.cc_init(n, s, d, stream=stream.cuda_stream)
     out = torch.empty(n, dtype=torch.int32, device=dev)
-    for _ in range(args.warmup):
-        cc.cc_run(g, out, args.order, mode, args.interval)
-    torch.cuda.synchronize()
+    edges = (n, s, d) if args.entry == "noalloc" else None
+    timed_runs(cc, g, out, args.warmup, args.order, mode, args.interval, stream, edges)
 
     sampler = ClockSampler(local)
     sampler.start()
     time.sleep(0.3)
     barrier(world)
     torch.cuda.synchronize()
-    ms, stats = timed_runs(cc, g, out, args.steps, args.order, mode, args.interval, stream)
+    ms, stats = timed_runs(cc, g, out, args.steps, args.order, mode, args.interval, stream, edges)
     torch.cuda.synchronize()
     barrier(world)
     clocks = sampler.stop()
@@ -273,7 +293,7 @@ def run_ours(args, rank, world, local):
     value = m * args.steps * world / (ms_max * 1e-3)
 
     sweeps = [st.sweeps for st in stats]
-    loop_ms = sum(st.loop_ms for st in stats)
+    loop_ms = sum(st.loop_ms for st in stats) if edges is None else ms
     tot_sweeps = sum(sweeps)
     B = 4
     per_sweep = 2 * B * m + B * n + (3 * B * n if mode == cc.CC_SYNC else 0)
@@ -362,7 +382,7 @@ def variants(cc, g, out, n, m, args, dev, seed, stream):
                               (4, cc.CC_SYNC, "o4-sync"), (0, cc.CC_ASYNC, "full-async"),
                               (1, cc.CC_ASYNC, "o1-async")]:
         res[f"{args.workload}/{name}"] = measure(g, out, n, m, order, mode, 1)
-    if args.workload != "grid4096":
+    if args.workload.startswith("rmat"):
         n2, s2, d2, _ = make_workload("grid4096", dev, seed)
         g2 = cc.cc_init(n2, s2, d2, stream=stream.cuda_stream)
         o2 = torch.empty(n2, dtype=torch.int32, device=dev)

@@ -166,24 +166,24 @@ static int grid_for(K kernel, int64_t work_items) {
 
 template <int H, bool SYNC, typename IdT>
 static cudaError_t launch_sweep_t(const cc_graph* g, IdT* L, IdT* Lu, int h, int32_t* flag,
-                                  cudaStream_t s) {
+                                  int first, cudaStream_t s) {
     constexpr int G = (H == 1) ? 2 : 1;  // edge groups of 4 per thread per step
     auto k = cc::mm_sweep_kernel<H, SYNC, G, IdT>;
     const int grid = grid_for(k, g->m / (4 * G) + 1);
     k<<<grid, kThreads, 0, s>>>(static_cast<const IdT*>(g->src), static_cast<const IdT*>(g->dst),
-                                 g->m, L, Lu, h, flag);
+                                 g->m, L, Lu, h, flag, g->ctl, first);
     return cudaGetLastError();
 }
 
 template <bool SYNC, typename IdT>
 static cudaError_t launch_sweep_m(const cc_graph* g, int order, IdT* L, IdT* Lu, int32_t* flag,
-                                  cudaStream_t s) {
+                                  int first, cudaStream_t s) {
     switch (order) {
-        case 1: return launch_sweep_t<1, SYNC, IdT>(g, L, Lu, 1, flag, s);
-        case 2: return launch_sweep_t<2, SYNC, IdT>(g, L, Lu, 2, flag, s);
-        case 4: return launch_sweep_t<4, SYNC, IdT>(g, L, Lu, 4, flag, s);
-        case CC_ORDER_FULL: return launch_sweep_t<0, SYNC, IdT>(g, L, Lu, cc::kFullChainHops, flag, s);
-        default: return launch_sweep_t<0, SYNC, IdT>(g, L, Lu, order, flag, s);
+        case 1: return launch_sweep_t<1, SYNC, IdT>(g, L, Lu, 1, flag, first, s);
+        case 2: return launch_sweep_t<2, SYNC, IdT>(g, L, Lu, 2, flag, first, s);
+        case 4: return launch_sweep_t<4, SYNC, IdT>(g, L, Lu, 4, flag, first, s);
+        case CC_ORDER_FULL: return launch_sweep_t<0, SYNC, IdT>(g, L, Lu, cc::kFullChainHops, flag, first, s);
+        default: return launch_sweep_t<0, SYNC, IdT>(g, L, Lu, order, flag, first, s);
     }
 }
 
@@ -201,8 +201,12 @@ static cudaError_t enqueue_block(cc_graph* g, int order, int mode, int c, IdT* L
                                  cudaGraphConditionalHandle loop, cudaStream_t s) {
     for (int j = 0; j < c; ++j) {
         int32_t* flag = (j == c - 1) ? &g->ctl->flag : nullptr;
-        cudaError_t e = (mode == CC_SYNC) ? launch_sweep_m<true, IdT>(g, order, L, Lu, flag, s)
-                                          : launch_sweep_m<false, IdT>(g, order, L, nullptr, flag, s);
+        // synchronous runs start with the gather-free identity sweep (the
+        // first iteration of Alg. 1, exactly); asynchronous runs gain more
+        // from reading labels that other edges have already lowered
+        const int first = (j == 0 && mode == CC_SYNC) ? 1 : 0;
+        cudaError_t e = (mode == CC_SYNC) ? launch_sweep_m<true, IdT>(g, order, L, Lu, flag, first, s)
+                                          : launch_sweep_m<false, IdT>(g, order, L, nullptr, flag, first, s);
         if (e != cudaSuccess) return e;
         if (mode == CC_SYNC) {
             e = launch_copy<IdT>(L, Lu, g->n, s);
@@ -339,16 +343,14 @@ static cc_status init_edges(cc_graph* g, int layout, const void* a, const void* 
     // every endpoint must lie in [0, n)
     if (cnt) {
         auto kv = cc::validate_ids_kernel<IdT>;
-        const int grid = grid_for(kv, cnt);
-        kv<<<grid, kThreads, 0, s>>>(static_cast<const IdT*>(g->src), cnt, n, g->ctl);
-        CC_LAUNCHED();
-        kv<<<grid, kThreads, 0, s>>>(static_cast<const IdT*>(g->dst), cnt, n, g->ctl);
+        kv<<<grid_for(kv, cnt / 4 + 1), kThreads, 0, s>>>(static_cast<const IdT*>(g->src),
+                                                            static_cast<const IdT*>(g->dst), cnt, n, g->ctl);
         CC_LAUNCHED();
     }
     CC_CUDA(cudaMemcpyAsync(g->ctl_h, g->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
     CC_CUDA(cudaStreamSynchronize(s));
     if (g->ctl_h->bad_count)
-        return set_error(CC_EIDRANGE, "%llu edge endpoints outside [0, %lld) (first at entry %llu of src or dst)",
+        return set_error(CC_EIDRANGE, "%llu edge endpoints outside [0, %lld) (first at edge %llu)",
                          g->ctl_h->bad_count, (long long)n, g->ctl_h->first_bad);
     return CC_OK;
 }
@@ -386,7 +388,7 @@ extern "C" cc_status cc_init(cc_graph** out, int64_t n, int id_bits, int layout,
         if (e == cudaSuccess) e = cudaEventCreate(&g->evl1);
         if (e != cudaSuccess) return fail(cuda_fail(e, "cc_init allocation", __FILE__, __LINE__));
     }
-    cc::ctl_reset_kernel<<<1, 32, 0, s>>>(g->ctl, 1);
+    cc::ctl_reset_kernel<<<1, 32, 0, s>>>(g->ctl, 1, 0);
     if (cudaGetLastError() != cudaSuccess) return fail(set_error(CC_ECUDA, "cc_init: launch failed"));
     st = (id_bits == 64) ? init_edges<int64_t>(g, layout, a, b, cnt, on_device, s)
                          : init_edges<int32_t>(g, layout, a, b, cnt, on_device, s);
@@ -482,7 +484,7 @@ static cc_status run_impl(cc_graph* g, int order, int mode, int c, int32_t max_s
     }
 
     CC_CUDA(cudaEventRecord(g->ev0, s));
-    cc::ctl_reset_kernel<<<1, 32, 0, s>>>(g->ctl, max_sweeps);
+    cc::ctl_reset_kernel<<<1, 32, 0, s>>>(g->ctl, max_sweeps, init_labels ? 0 : 1);
     CC_LAUNCHED();
     CC_CUDA(g->id_bits == 64 ? enqueue_init<int64_t>(g, (int64_t*)L, (int64_t*)Lu, init_labels, s)
                              : enqueue_init<int32_t>(g, (int32_t*)L, (int32_t*)Lu, init_labels, s));

@@ -62,21 +62,22 @@ int grid_for(K kernel, int64_t items) {
 
 template <int H, bool SYNC>
 void sweep_t(const int32_t* src, const int32_t* dst, int64_t m, int32_t* L, int32_t* Lu, int h,
-             int32_t* flag, cudaStream_t s) {
+             int32_t* flag, int first, cudaStream_t s) {
     constexpr int G = (H == 1) ? 2 : 1;
     auto k = cc::mm_sweep_kernel<H, SYNC, G, int32_t>;
-    k<<<grid_for(k, m / (4 * G) + 1), kThreads, 0, s>>>(src, dst, m, L, Lu, h, flag);
+    k<<<grid_for(k, m / (4 * G) + 1), kThreads, 0, s>>>(src, dst, m, L, Lu, h, flag, nullptr, first);
 }
 
+// first == 2 selects the identity sweep (the run's first sweep); 0 otherwise.
 template <bool SYNC>
 void sweep(int order, const int32_t* src, const int32_t* dst, int64_t m, int32_t* L, int32_t* Lu,
-           int32_t* flag, cudaStream_t s) {
+           int32_t* flag, int first, cudaStream_t s) {
     switch (order) {
-        case 1: sweep_t<1, SYNC>(src, dst, m, L, Lu, 1, flag, s); break;
-        case 2: sweep_t<2, SYNC>(src, dst, m, L, Lu, 2, flag, s); break;
-        case 4: sweep_t<4, SYNC>(src, dst, m, L, Lu, 4, flag, s); break;
-        case CC_ORDER_FULL: sweep_t<0, SYNC>(src, dst, m, L, Lu, cc::kFullChainHops, flag, s); break;
-        default: sweep_t<0, SYNC>(src, dst, m, L, Lu, order, flag, s); break;
+        case 1: sweep_t<1, SYNC>(src, dst, m, L, Lu, 1, flag, first, s); break;
+        case 2: sweep_t<2, SYNC>(src, dst, m, L, Lu, 2, flag, first, s); break;
+        case 4: sweep_t<4, SYNC>(src, dst, m, L, Lu, 4, flag, first, s); break;
+        case CC_ORDER_FULL: sweep_t<0, SYNC>(src, dst, m, L, Lu, cc::kFullChainHops, flag, first, s); break;
+        default: sweep_t<0, SYNC>(src, dst, m, L, Lu, order, flag, first, s); break;
     }
 }
 
@@ -118,12 +119,11 @@ extern "C" cc_status cc_run_noalloc(int64_t n, const int32_t* src, const int32_t
     Ctl h;
 
     // the scratch keeps the previous call's contents: clear the control words
-    cc::ctl_reset_kernel<<<1, 32, 0, s>>>(ctl, max_sweeps);
+    cc::ctl_reset_kernel<<<1, 32, 0, s>>>(ctl, max_sweeps, 1);
     NA_CUDA(cudaGetLastError());
     if (m > 0) {
         auto kv = cc::validate_ids_kernel<int32_t>;
-        kv<<<grid_for(kv, m), kThreads, 0, s>>>(src, m, n, ctl);
-        kv<<<grid_for(kv, m), kThreads, 0, s>>>(dst, m, n, ctl);
+        kv<<<grid_for(kv, m / 4 + 1), kThreads, 0, s>>>(src, dst, m, n, ctl);
         NA_CUDA(cudaGetLastError());
         NA_CUDA(cudaMemcpyAsync(&h, ctl, sizeof h, cudaMemcpyDeviceToHost, s));
         NA_CUDA(cudaStreamSynchronize(s));
@@ -140,12 +140,13 @@ extern "C" cc_status cc_run_noalloc(int64_t n, const int32_t* src, const int32_t
     while (true) {
         for (int j = 0; j < check_interval; ++j) {
             int32_t* flag = (j == check_interval - 1) ? &ctl->flag : nullptr;
+            const int first = (sweeps == 0 && j == 0 && mode == CC_SYNC) ? 2 : 0;
             if (mode == CC_SYNC) {
-                sweep<true>(order, src, dst, m, labels_out, Lu, flag, s);
+                sweep<true>(order, src, dst, m, labels_out, Lu, flag, first, s);
                 auto kc = cc::copy_kernel<int32_t>;
                 kc<<<grid_for(kc, n / 4 + 1), kThreads, 0, s>>>(labels_out, Lu, n);
             } else {
-                sweep<false>(order, src, dst, m, labels_out, nullptr, flag, s);
+                sweep<false>(order, src, dst, m, labels_out, nullptr, flag, first, s);
             }
         }
         NA_CUDA(cudaGetLastError());
