@@ -176,6 +176,65 @@ cc_status cc_run_noalloc(int64_t n, const int32_t *src, const int32_t *dst, int6
                          int mode, int check_interval, int32_t max_sweeps, int32_t *labels_out,
                          int32_t *sweeps_out, void *cuda_stream);
 
+/*
+ * Batched solve: many independent graphs in one CUDA-graph launch.
+ *
+ * The graphs are concatenated: graph g owns vertices [vtx_off[g], vtx_off[g+1])
+ * and edges [edge_off[g], edge_off[g+1]) of src/dst, and its edge ids are
+ * LOCAL (0 .. n_g-1).  Each graph runs its own Contour iteration -- Alg. 1 or
+ * the asynchronous variant of Section III-B, with its own convergence flag
+ * (Section III-B2) and sweep count -- so every label is the smallest LOCAL id
+ * of the vertex's component within its own graph.
+ *
+ * Small graphs (labels fit the shared-memory budget) are solved whole by one
+ * CTA each with their labels in shared memory; large graphs advance one sweep
+ * per round, all active large graphs together, until each has converged.  An
+ * autotuner chooses the shared-memory budget, CTA size and edges per thread
+ * of the small-graph kernel by timing candidates on the batch itself and
+ * caches the choice per size histogram.
+ *
+ * cc_batch_init   vtx_off, edge_off: HOST int64 arrays of n_graphs+1 entries
+ *                 (non-decreasing, starting at 0); src, dst: DEVICE int32
+ *                 arrays of edge_off[n_graphs] local ids, borrowed (must stay
+ *                 alive and unchanged until cc_batch_free).  Every id is
+ *                 checked on the device (CC_EIDRANGE).  autotune: 0 = defaults,
+ *                 1 = tune (or reuse a cached tuning), 2 = always re-tune.
+ * cc_batch_run    one schedule for every graph (order, mode, check_interval as
+ *                 for cc_run), or order == CC_ORDER_AUTO for a per-graph
+ *                 schedule chosen by the learned scheduler (the plain order-2
+ *                 synchronous schedule without loaded weights).  labels_out:
+ *                 DEVICE int32[vtx_off[n_graphs]]; sweeps_out: HOST int32
+ *                 [n_graphs] or NULL; solve_ms: NULL or the device time.
+ *                 CC_ENOTCONVERGED if a graph reached max_sweeps.
+ *                 Synchronises the plan's stream.
+ * cc_batch_set_schedule / cc_batch_run_scheduled   an explicit per-graph
+ *                 schedule (HOST arrays of n_graphs entries).
+ * cc_batch        one-shot init + run + free (no autotuning; sweeps_out HOST).
+ */
+typedef struct cc_batch_plan cc_batch_plan;
+
+cc_status cc_batch_init(cc_batch_plan **b, int32_t n_graphs, const int64_t *vtx_off,
+                        const int64_t *edge_off, const int32_t *src, const int32_t *dst, int autotune,
+                        void *cuda_stream);
+cc_status cc_batch_run(cc_batch_plan *b, int order, int mode, int check_interval, int32_t max_sweeps,
+                       int32_t *labels_out, int32_t *sweeps_out, double *solve_ms);
+cc_status cc_batch_set_schedule(cc_batch_plan *b, const int32_t *order, const int32_t *mode,
+                                const int32_t *check_interval);
+cc_status cc_batch_run_scheduled(cc_batch_plan *b, int32_t max_sweeps, int32_t *labels_out,
+                                 int32_t *sweeps_out, double *solve_ms);
+cc_status cc_batch_tuning(const cc_batch_plan *b, int32_t *smem_budget, int32_t *threads,
+                          int32_t *edges_per_thread);
+/* Override the small-graph kernel's tuning: smem_budget bytes of shared
+ * memory per CTA (graphs whose labels do not fit take the large-graph path;
+ * 0 sends every non-empty graph there), threads in {256, 512, 1024}, edges
+ * per thread 1..4. */
+cc_status cc_batch_set_tuning(cc_batch_plan *b, int32_t smem_budget, int32_t threads,
+                              int32_t edges_per_thread);
+void cc_batch_free(cc_batch_plan *b);
+cc_status cc_batch(int32_t n_graphs, const int64_t *vtx_off, const int64_t *edge_off,
+                   const int32_t *src, const int32_t *dst, int order, int mode, int check_interval,
+                   int32_t *labels_out, int32_t *sweeps_out, void *cuda_stream);
+
 /* Make later cc_run calls on g enqueue on another stream (default: the stream
  * passed to cc_init). */
 cc_status cc_graph_set_stream(cc_graph *g, void *cuda_stream);

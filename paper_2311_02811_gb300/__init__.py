@@ -18,7 +18,9 @@ __all__ = [
     "CC_OK", "CC_EINVAL", "CC_EIDRANGE", "CC_ENOMEM", "CC_ECUDA", "CC_ENOTCONVERGED",
     "CC_ETIMEOUT", "CC_ID32", "CC_ID64", "CC_COO", "CC_CSR", "CC_SYNC", "CC_ASYNC",
     "CC_ORDER_FULL", "CC_ORDER_AUTO", "CC_NOALLOC_MAX_N", "CCError", "cc_stats", "cc_graph", "lib", "LIB_PATH",
-    "cc_init", "cc_run", "cc_run_noalloc", "cc_free", "cc_graph_info", "cc_graph_set_stream", "cc_strerror",
+    "cc_init", "cc_run", "cc_run_noalloc", "cc_free", "cc_batch_plan", "cc_batch_init",
+    "cc_batch_run", "cc_batch_set_schedule", "cc_batch_run_scheduled", "cc_batch_tuning",
+    "cc_batch_set_tuning", "cc_batch_free", "cc_batch", "cc_graph_info", "cc_graph_set_stream", "cc_strerror",
     "cc_last_error",
 ]
 
@@ -186,6 +188,125 @@ def cc_run_noalloc(n, src, dst, labels_out, order=2, mode=CC_ASYNC, check_interv
         _check(rc, "cc_run_noalloc")
         return sw.value
     return rc, sw.value
+
+
+lib.cc_batch_init.argtypes = [ctypes.POINTER(_p), _i32, _p, _p, _p, _p, _int, _p]
+lib.cc_batch_init.restype = _int
+lib.cc_batch_run.argtypes = [_p, _int, _int, _int, _i32, _p, _p, ctypes.POINTER(ctypes.c_double)]
+lib.cc_batch_run.restype = _int
+lib.cc_batch_set_schedule.argtypes = [_p, _p, _p, _p]
+lib.cc_batch_set_schedule.restype = _int
+lib.cc_batch_run_scheduled.argtypes = [_p, _i32, _p, _p, ctypes.POINTER(ctypes.c_double)]
+lib.cc_batch_run_scheduled.restype = _int
+lib.cc_batch_tuning.argtypes = [_p, ctypes.POINTER(_i32), ctypes.POINTER(_i32), ctypes.POINTER(_i32)]
+lib.cc_batch_tuning.restype = _int
+lib.cc_batch_set_tuning.argtypes = [_p, _i32, _i32, _i32]
+lib.cc_batch_set_tuning.restype = _int
+lib.cc_batch_free.argtypes = [_p]
+lib.cc_batch_free.restype = None
+lib.cc_batch.argtypes = [_i32, _p, _p, _p, _p, _int, _int, _int, _p, _p, _p]
+lib.cc_batch.restype = _int
+
+
+class cc_batch_plan:
+    """A cc_batch_plan* handle; keeps the borrowed device edge arrays alive."""
+
+    def __init__(self, ptr, n_graphs, total_n, keep):
+        self._as_parameter_ = _p(ptr)
+        self.n_graphs = n_graphs
+        self.total_n = total_n
+        self._keep = keep
+
+
+def _i64_host(a):
+    import numpy as np
+    if hasattr(a, "detach"):
+        a = a.detach().cpu().numpy()
+    return np.ascontiguousarray(np.asarray(a), dtype=np.int64)
+
+
+def _i32_host(a):
+    import numpy as np
+    if hasattr(a, "detach"):
+        a = a.detach().cpu().numpy()
+    return np.ascontiguousarray(np.asarray(a), dtype=np.int32)
+
+
+def cc_batch_init(vtx_off, edge_off, src, dst, autotune=0, stream=None):
+    """Plan a batched solve (offsets on the host, edges on the device)."""
+    vo, eo = _i64_host(vtx_off), _i64_host(edge_off)
+    ps, _ = _ptr(src)
+    pd, _ = _ptr(dst)
+    b = _p()
+    G = len(vo) - 1
+    _check(lib.cc_batch_init(ctypes.byref(b), G, vo.ctypes.data, eo.ctypes.data, ps, pd,
+                             int(autotune), _stream(stream)), "cc_batch_init")
+    return cc_batch_plan(b.value, G, int(vo[-1]) if G else 0, (src, dst))
+
+
+def cc_batch_run(b, labels_out, order=2, mode=CC_ASYNC, check_interval=1, max_sweeps=1 << 20,
+                 raise_on_error=True):
+    """Solve every graph of the plan; returns (sweeps per graph, solve_ms)."""
+    import numpy as np
+    po, _ = _ptr(labels_out)
+    sweeps = np.zeros(b.n_graphs, dtype=np.int32)
+    ms = ctypes.c_double(0.0)
+    rc = lib.cc_batch_run(b, int(order), int(mode), int(check_interval), int(max_sweeps), po,
+                          sweeps.ctypes.data, ctypes.byref(ms))
+    if raise_on_error:
+        _check(rc, "cc_batch_run")
+        return sweeps, ms.value
+    return rc, sweeps, ms.value
+
+
+def cc_batch_set_schedule(b, order, mode, check_interval):
+    o, m_, c = _i32_host(order), _i32_host(mode), _i32_host(check_interval)
+    _check(lib.cc_batch_set_schedule(b, o.ctypes.data, m_.ctypes.data, c.ctypes.data),
+           "cc_batch_set_schedule")
+
+
+def cc_batch_run_scheduled(b, labels_out, max_sweeps=1 << 20, raise_on_error=True):
+    import numpy as np
+    po, _ = _ptr(labels_out)
+    sweeps = np.zeros(b.n_graphs, dtype=np.int32)
+    ms = ctypes.c_double(0.0)
+    rc = lib.cc_batch_run_scheduled(b, int(max_sweeps), po, sweeps.ctypes.data, ctypes.byref(ms))
+    if raise_on_error:
+        _check(rc, "cc_batch_run_scheduled")
+        return sweeps, ms.value
+    return rc, sweeps, ms.value
+
+
+def cc_batch_tuning(b):
+    x, y, z = _i32(), _i32(), _i32()
+    _check(lib.cc_batch_tuning(b, ctypes.byref(x), ctypes.byref(y), ctypes.byref(z)), "cc_batch_tuning")
+    return x.value, y.value, z.value
+
+
+def cc_batch_set_tuning(b, smem_budget, threads=512, edges_per_thread=4):
+    _check(lib.cc_batch_set_tuning(b, int(smem_budget), int(threads), int(edges_per_thread)),
+           "cc_batch_set_tuning")
+
+
+def cc_batch_free(b):
+    lib.cc_batch_free(b)
+    if isinstance(b, cc_batch_plan):
+        b._as_parameter_ = _p(None)
+        b._keep = ()
+
+
+def cc_batch(vtx_off, edge_off, src, dst, labels_out, order=2, mode=CC_ASYNC, check_interval=1,
+             stream=None):
+    """One-shot batched solve; returns the sweeps per graph."""
+    import numpy as np
+    vo, eo = _i64_host(vtx_off), _i64_host(edge_off)
+    ps, _ = _ptr(src)
+    pd, _ = _ptr(dst)
+    po, _ = _ptr(labels_out)
+    sweeps = np.zeros(len(vo) - 1, dtype=np.int32)
+    _check(lib.cc_batch(len(vo) - 1, vo.ctypes.data, eo.ctypes.data, ps, pd, int(order), int(mode),
+                        int(check_interval), po, sweeps.ctypes.data, _stream(stream)), "cc_batch")
+    return sweeps
 
 
 def cc_graph_info(g):

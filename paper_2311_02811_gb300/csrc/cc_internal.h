@@ -3,6 +3,8 @@
 
 #include <cuda_runtime.h>
 
+#include <stdint.h>
+
 #include "../../include/contour.h"
 
 namespace cc {
@@ -21,5 +23,18 @@ cc_status graph_nm(const cc_graph* g, long long* n, long long* m);
 // CC_ORDER_AUTO: pick (order, mode, check interval) for a graph; the plain
 // order-2 synchronous schedule with c = 1 when no scheduler weights are loaded.
 cc_status resolve_schedule(cc_graph* g, int* order, int* mode, int* c);
+
+// Batched path (batch.cu) and its schedule resolution (sched.cu).
+cc_status batch_solve(cc_batch_plan* b, int32_t max_sweeps, int32_t* labels_out, int32_t* sweeps_out,
+                      double* solve_ms);
+cc_status batch_resolve_schedule(cc_batch_plan* b, int mode, int c);
+cc_status batch_autotune(cc_batch_plan* b, int force);
+int32_t batch_graph_count(const cc_batch_plan* b);
+const int64_t* batch_off_v(const cc_batch_plan* b);
+const int64_t* batch_off_e(const cc_batch_plan* b);
+const int32_t* batch_src(const cc_batch_plan* b);
+const int32_t* batch_dst(const cc_batch_plan* b);
+cudaStream_t batch_stream(const cc_batch_plan* b);
+void batch_set_schedule(cc_batch_plan* b, const int32_t* h, const int32_t* sync, const int32_t* c);
 
 }  // namespace cc
