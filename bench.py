@@ -393,12 +393,88 @@ def variants(cc, g, out, n, m, args, dev, seed, stream):
     return res
 
 
+def make_batch(n_graphs: int, device, seed: int):
+    t0 = time.perf_counter()
+    vo, eo, s, d, params = gg.batch_mix(n_graphs, seed=seed, device=device)
+    torch.cuda.synchronize()
+    return vo.numpy(), eo.numpy(), s, d, params, time.perf_counter() - t0
+
+
+def run_batch(args, rank, world, local):
+    """Batched solve of the batch mix vs one cc_run per graph, identical output."""
+    import paper_2311_02811_gb300 as cc
+    dev = torch.device("cuda", torch.cuda.current_device())
+    G = int(args.workload[5:])
+    vo, eo, s, d, params, gen_s = make_batch(G, dev, gg.BASE_SEED + 3 + rank)
+    torch.cuda.empty_cache()
+    total_n, total_m = int(vo[-1]), int(eo[-1])
+    stream = torch.cuda.current_stream()
+    mode = cc.CC_ASYNC if args.mode == "async" else cc.CC_SYNC
+    t0 = time.perf_counter()
+    plan = cc.cc_batch_init(vo, eo, s, d, autotune=1, stream=stream.cuda_stream)
+    tune_s = time.perf_counter() - t0
+    out_b = torch.empty(total_n, dtype=torch.int32, device=dev)
+    res = {}
+
+    def timed(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    for order, md, name in [(args.order, mode, "batched"), (2, cc.CC_SYNC, "batched-o2-sync"),
+                            (0, cc.CC_ASYNC, "batched-full-async")]:
+        ms = timed(lambda: cc.cc_batch_run(plan, out_b, order, md, args.interval), args.steps)
+        res[name] = {"ms": ms, "edges_per_s": total_m / (ms * 1e-3)}
+    cc.cc_batch_run(plan, out_b, args.order, mode, args.interval)
+    ref = out_b.clone()
+    # plain form: one handle per graph, one cc_run per graph
+    handles = []
+    for g in range(G):
+        a, b = int(eo[g]), int(eo[g + 1])
+        handles.append((cc.cc_init(int(vo[g + 1] - vo[g]), s[a:b], d[a:b], stream=stream.cuda_stream),
+                        int(vo[g]), int(vo[g + 1])))
+    out_p = torch.empty(total_n, dtype=torch.int32, device=dev)
+
+    def plain(order, md):
+        for h, v0, v1 in handles:
+            cc.cc_run(h, out_p[v0:v1], order, md, 1)
+
+    for order, md, name in [(2, cc.CC_SYNC, "plain-o2-sync"), (args.order, mode, "plain")]:
+        ms = timed(lambda: plain(order, md), max(1, min(args.steps, 3)))
+        res[name] = {"ms": ms, "edges_per_s": total_m / (ms * 1e-3)}
+    identical = bool(torch.equal(out_p, ref))
+    for h, _, _ in handles:
+        cc.cc_free(h)
+    tuning = cc.cc_batch_tuning(plan)
+    cc.cc_batch_free(plan)
+    line = {"metric": "CC edges/sec (m / solve time), batched vs plain", "value": res["batched"]["edges_per_s"],
+            "unit": "edges/s", "n_gpus": world, "steps": args.steps, "warmup": 1,
+            "ms_per_step": res["batched"]["ms"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": f"batch-mix-{G}", "graphs": G, "n": total_n, "m": total_m,
+                       "order": args.order, "mode": args.mode, "check_interval": args.interval,
+                       "generation_s": gen_s, "plan_and_autotune_s": tune_s,
+                       "tuning": {"smem_budget": tuning[0], "threads": tuning[1], "edges_per_thread": tuning[2]}},
+            "forms": res, "identical_output": identical}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     rank, world, local = dist_init()
     try:
         if args.impl == "reference":
             run_reference(args, rank, world)
+        elif args.workload.startswith("batch"):
+            run_batch(args, rank, world, local)
         else:
             run_ours(args, rank, world, local)
     finally:

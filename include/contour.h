@@ -235,6 +235,57 @@ cc_status cc_batch(int32_t n_graphs, const int64_t *vtx_off, const int64_t *edge
                    const int32_t *src, const int32_t *dst, int order, int mode, int check_interval,
                    int32_t *labels_out, int32_t *sweeps_out, void *cuda_stream);
 
+/*
+ * Learned schedule selection (CC_ORDER_AUTO).
+ *
+ * The paper chooses operators by hand from graph size and diameter (Section
+ * IV-E: C-1 for small low-diameter graphs, C-m for large or long-diameter
+ * ones, C-2 as the stable default).  Here a small MLP learns the choice from
+ * measured solve times.  All schedules return identical labels.
+ *
+ * Features (CC_SCHED_FEATURES floats per graph, each log2(1 + x)): n, m, the
+ * degree variance and maximum degree estimated on an edge sample (all edges
+ * when m <= 16384, else the 16384 edges at positions floor(j*m/16384),
+ * counts scaled by m/16384), and the eccentricities of 8 sources in the
+ * sampled graph (the src endpoints of sample positions floor((2i+1)*S/16)),
+ * by breadth-first search capped at 16 levels.
+ * Model: 12 -> 64 -> 64 -> 64 -> CC_SCHED_CLASSES, ReLU, standardised inputs;
+ * BF16 weights, FP32 biases and accumulation.  Class k decodes to
+ * order {2, 4, CC_ORDER_FULL}[k/6], mode (k/3)%2 (0 sync, 1 async) and check
+ * interval {1, 2, 4}[k%3].
+ *
+ * cc_sched_load        install a weight blob (cc_sched_blob_bytes() bytes, format
+ *                      "CCMLP01": header with feature mean/std, then per layer
+ *                      BF16 weights [out][in] and FP32 biases); NULL unloads and
+ *                      restores the plain order-2 synchronous fallback.  The model
+ *                      is process-wide.
+ * cc_graph_features / cc_batch_features   features of a graph / every graph of
+ *                      a plan (int32 ids), written to HOST memory.
+ * cc_sched_predict     classes (and optionally CC_SCHED_CLASSES logits) for
+ *                      count HOST feature rows; CC_EINVAL without weights.
+ * cc_sched_train       train the MLP on the GPU (mini-batch Adam, softmax cross-
+ *                      entropy) on N HOST rows with labels in [0, 18); inputs are
+ *                      standardised with their own mean/std; parameters start at
+ *                      init_params (cc_sched_param_count() FP32 values, per layer
+ *                      weights [out][in] then biases) or, if NULL, at a He-uniform
+ *                      draw from SplitMix64(seed).  Writes a blob to blob_out.
+ * cc_sched_train_step  one Adam step (t = 1, zero moments, lr) on B standardised
+ *                      rows, updating params_inout in place; for testing.
+ */
+enum { CC_SCHED_FEATURES = 12, CC_SCHED_CLASSES = 18 };
+cc_status cc_sched_load(const void *weights, size_t bytes);
+size_t cc_sched_blob_bytes(void);
+int32_t cc_sched_param_count(void);
+cc_status cc_sched_decode(int32_t cls, int *order, int *mode, int *check_interval);
+cc_status cc_graph_features(cc_graph *g, float *features_out);
+cc_status cc_batch_features(cc_batch_plan *b, float *features_out);
+cc_status cc_sched_predict(const float *features, int32_t count, int32_t *cls_out, float *logits_out);
+cc_status cc_sched_train(const float *features, const int32_t *labels, int32_t N,
+                         const float *init_params, int32_t epochs, int32_t batch, float lr,
+                         uint64_t seed, void *blob_out, float *final_loss);
+cc_status cc_sched_train_step(const float *features_norm, const int32_t *labels, int32_t B,
+                              float *params_inout, float lr, float *loss_out);
+
 /* Make later cc_run calls on g enqueue on another stream (default: the stream
  * passed to cc_init). */
 cc_status cc_graph_set_stream(cc_graph *g, void *cuda_stream);

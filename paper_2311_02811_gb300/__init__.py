@@ -20,7 +20,9 @@ __all__ = [
     "CC_ORDER_FULL", "CC_ORDER_AUTO", "CC_NOALLOC_MAX_N", "CCError", "cc_stats", "cc_graph", "lib", "LIB_PATH",
     "cc_init", "cc_run", "cc_run_noalloc", "cc_free", "cc_batch_plan", "cc_batch_init",
     "cc_batch_run", "cc_batch_set_schedule", "cc_batch_run_scheduled", "cc_batch_tuning",
-    "cc_batch_set_tuning", "cc_batch_free", "cc_batch", "cc_graph_info", "cc_graph_set_stream", "cc_strerror",
+    "cc_batch_set_tuning", "cc_batch_free", "cc_batch", "cc_sched_load", "cc_sched_blob_bytes",
+    "cc_sched_param_count", "cc_sched_decode", "cc_graph_features", "cc_batch_features",
+    "cc_sched_predict", "cc_sched_train", "cc_sched_train_step", "CC_SCHED_FEATURES", "CC_SCHED_CLASSES", "cc_graph_info", "cc_graph_set_stream", "cc_strerror",
     "cc_last_error",
 ]
 
@@ -307,6 +309,100 @@ def cc_batch(vtx_off, edge_off, src, dst, labels_out, order=2, mode=CC_ASYNC, ch
     _check(lib.cc_batch(len(vo) - 1, vo.ctypes.data, eo.ctypes.data, ps, pd, int(order), int(mode),
                         int(check_interval), po, sweeps.ctypes.data, _stream(stream)), "cc_batch")
     return sweeps
+
+
+CC_SCHED_FEATURES, CC_SCHED_CLASSES = 12, 18
+_f = ctypes.c_float
+lib.cc_sched_load.argtypes = [_p, ctypes.c_size_t]
+lib.cc_sched_load.restype = _int
+lib.cc_sched_blob_bytes.argtypes = []
+lib.cc_sched_blob_bytes.restype = ctypes.c_size_t
+lib.cc_sched_param_count.argtypes = []
+lib.cc_sched_param_count.restype = _i32
+lib.cc_sched_decode.argtypes = [_i32, ctypes.POINTER(_int), ctypes.POINTER(_int), ctypes.POINTER(_int)]
+lib.cc_sched_decode.restype = _int
+lib.cc_graph_features.argtypes = [_p, _p]
+lib.cc_graph_features.restype = _int
+lib.cc_batch_features.argtypes = [_p, _p]
+lib.cc_batch_features.restype = _int
+lib.cc_sched_predict.argtypes = [_p, _i32, _p, _p]
+lib.cc_sched_predict.restype = _int
+lib.cc_sched_train.argtypes = [_p, _p, _i32, _p, _i32, _i32, _f, ctypes.c_uint64, _p, ctypes.POINTER(_f)]
+lib.cc_sched_train.restype = _int
+lib.cc_sched_train_step.argtypes = [_p, _p, _i32, _p, _f, ctypes.POINTER(_f)]
+lib.cc_sched_train_step.restype = _int
+
+
+def cc_sched_load(blob):
+    """Install scheduler weights (bytes); None restores the plain fallback."""
+    if blob is None:
+        _check(lib.cc_sched_load(None, 0), "cc_sched_load")
+        return
+    buf = ctypes.create_string_buffer(bytes(blob), len(blob))
+    _check(lib.cc_sched_load(buf, len(blob)), "cc_sched_load")
+
+
+def cc_sched_blob_bytes():
+    return lib.cc_sched_blob_bytes()
+
+
+def cc_sched_param_count():
+    return lib.cc_sched_param_count()
+
+
+def cc_sched_decode(cls):
+    o, m_, c = _int(), _int(), _int()
+    _check(lib.cc_sched_decode(int(cls), ctypes.byref(o), ctypes.byref(m_), ctypes.byref(c)), "cc_sched_decode")
+    return o.value, m_.value, c.value
+
+
+def cc_graph_features(g):
+    import numpy as np
+    out = np.zeros(CC_SCHED_FEATURES, dtype=np.float32)
+    _check(lib.cc_graph_features(g, out.ctypes.data), "cc_graph_features")
+    return out
+
+
+def cc_batch_features(b):
+    import numpy as np
+    out = np.zeros((b.n_graphs, CC_SCHED_FEATURES), dtype=np.float32)
+    _check(lib.cc_batch_features(b, out.ctypes.data), "cc_batch_features")
+    return out
+
+
+def cc_sched_predict(features):
+    import numpy as np
+    f = np.ascontiguousarray(features, dtype=np.float32).reshape(-1, CC_SCHED_FEATURES)
+    cls = np.zeros(len(f), dtype=np.int32)
+    logits = np.zeros((len(f), CC_SCHED_CLASSES), dtype=np.float32)
+    _check(lib.cc_sched_predict(f.ctypes.data, len(f), cls.ctypes.data, logits.ctypes.data), "cc_sched_predict")
+    return cls, logits
+
+
+def cc_sched_train(features, labels, epochs=60, batch=256, lr=2e-3, seed=1, init_params=None):
+    """Train the scheduler MLP on the GPU; returns (blob bytes, final mean loss)."""
+    import numpy as np
+    f = np.ascontiguousarray(features, dtype=np.float32).reshape(-1, CC_SCHED_FEATURES)
+    y = np.ascontiguousarray(labels, dtype=np.int32)
+    ip = None if init_params is None else np.ascontiguousarray(init_params, dtype=np.float32)
+    blob = ctypes.create_string_buffer(cc_sched_blob_bytes())
+    loss = _f(0)
+    _check(lib.cc_sched_train(f.ctypes.data, y.ctypes.data, len(f), None if ip is None else ip.ctypes.data,
+                              int(epochs), int(batch), float(lr), int(seed), blob, ctypes.byref(loss)),
+           "cc_sched_train")
+    return blob.raw, loss.value
+
+
+def cc_sched_train_step(features_std, labels, params, lr):
+    """One Adam step from zero moments; returns (new params, loss)."""
+    import numpy as np
+    f = np.ascontiguousarray(features_std, dtype=np.float32).reshape(-1, CC_SCHED_FEATURES)
+    y = np.ascontiguousarray(labels, dtype=np.int32)
+    p = np.array(params, dtype=np.float32)
+    loss = _f(0)
+    _check(lib.cc_sched_train_step(f.ctypes.data, y.ctypes.data, len(f), p.ctypes.data, float(lr),
+                                   ctypes.byref(loss)), "cc_sched_train_step")
+    return p, loss.value
 
 
 def cc_graph_info(g):

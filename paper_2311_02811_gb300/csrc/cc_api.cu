@@ -557,6 +557,7 @@ namespace cc {
 const void* graph_src(const cc_graph* g) { return g->src; }
 const void* graph_dst(const cc_graph* g) { return g->dst; }
 int graph_id_bits(const cc_graph* g) { return g->id_bits; }
+cudaStream_t graph_stream(const cc_graph* g) { return g->stream; }
 cc_status graph_nm(const cc_graph* g, long long* n, long long* m) {
     *n = g->n;
     *m = g->m;

@@ -19,6 +19,7 @@ const void* graph_src(const cc_graph* g);
 const void* graph_dst(const cc_graph* g);
 int graph_id_bits(const cc_graph* g);
 cc_status graph_nm(const cc_graph* g, long long* n, long long* m);
+cudaStream_t graph_stream(const cc_graph* g);
 
 // CC_ORDER_AUTO: pick (order, mode, check interval) for a graph; the plain
 // order-2 synchronous schedule with c = 1 when no scheduler weights are loaded.

@@ -57,3 +57,18 @@ def test_argument_errors_need_no_gpu(built_lib):
     assert cc.lib.cc_init(ctypes.byref(g), 4, 32, 0, None, None, 3, 0, None) == cc.CC_EINVAL
     assert "NULL" in cc.cc_last_error()
     assert cc.lib.cc_run(None, 2, 1, 1, 10, None, None, 0, None) == cc.CC_EINVAL
+
+
+def test_scheduler_host_side_without_gpu(built_lib):
+    """Class decoding and blob validation happen on the host."""
+    import paper_2311_02811_gb300 as cc
+    seen = set()
+    for k in range(cc.CC_SCHED_CLASSES):
+        o, m, c = cc.cc_sched_decode(k)
+        assert o == (2, 4, cc.CC_ORDER_FULL)[k // 6] and m == (k // 3) % 2 and c == (1, 2, 4)[k % 3]
+        seen.add((o, m, c))
+    assert len(seen) == 18
+    with pytest.raises(cc.CCError):
+        cc.cc_sched_decode(18)
+    assert cc.lib.cc_sched_load(b"not a blob", 10) == cc.CC_EINVAL
+    assert cc.cc_sched_blob_bytes() == 120 + 2 * (64 * 12 + 64 * 64 * 2 + 18 * 64) + 4 * (64 * 3 + 18)
