@@ -47,6 +47,10 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
+    p.add_argument("--batch-graphs", type=int, default=1024,
+                   help="also compare batched + learned vs plain on a batch-mix of this many graphs (0: off)")
+    p.add_argument("--reorder", choices=["none", "src", "lowdeg"], default="none",
+                   help="cc_graph_reorder layout step once before timing (included in e2e)")
     p.add_argument("--entry", choices=["cc_run", "noalloc"], default="cc_run",
                    help="cc_run (conditional CUDA-graph loop) or cc_run_noalloc (host-polled "
                         "plain launches of the same sweep kernel; profilers can see each sweep)")
@@ -76,6 +80,13 @@ def barrier(world):
     if world > 1:
         import torch.distributed as dist
         dist.barrier()
+
+
+def whole_job_rate(units_per_rank: float, ms_local: float, world: int):
+    """(units of all ranks per second, max ms over ranks): every rank solves the
+    same amount of work; the job takes as long as its slowest rank."""
+    ms = max_over_ranks(ms_local, world)
+    return units_per_rank * world / (ms * 1e-3), ms
 
 
 def max_over_ranks(x: float, world: int) -> float:
@@ -276,6 +287,12 @@ def run_ours(args, rank, world, local):
     m = s.numel()
     stream = torch.cuda.current_stream()
     g = cc.cc_init(n, s, d, stream=stream.cuda_stream)
+    reorder = {"none": 0, "src": cc.CC_REORDER_SRC, "lowdeg": cc.CC_REORDER_LOWDEG}[args.reorder]
+    reorder_ms = None
+    if reorder:
+        t0 = time.perf_counter()
+        cc.cc_graph_reorder(g, reorder)
+        reorder_ms = 1e3 * (time.perf_counter() - t0)
     out = torch.empty(n, dtype=torch.int32, device=dev)
     edges = (n, s, d) if args.entry == "noalloc" else None
     timed_runs(cc, g, out, args.warmup, args.order, mode, args.interval, stream, edges)
@@ -289,8 +306,7 @@ def run_ours(args, rank, world, local):
     torch.cuda.synchronize()
     barrier(world)
     clocks = sampler.stop()
-    ms_max = max_over_ranks(ms, world)
-    value = m * args.steps * world / (ms_max * 1e-3)
+    value, ms_max = whole_job_rate(m * args.steps, ms, world)
 
     sweeps = [st.sweeps for st in stats]
     loop_ms = sum(st.loop_ms for st in stats) if edges is None else ms
@@ -311,6 +327,9 @@ def run_ours(args, rank, world, local):
         "config": dict(cfg, n=n, m=m, order=args.order, mode=args.mode, check_interval=args.interval,
                        ids="int32", parallelism=f"replicas x{world}" if world > 1 else "single GPU",
                        l2="inputs larger than L2: edge list %.2f GB streamed every sweep" % (8 * m / 1e9),
+                       edge_order=("as generated (shuffled)" if not reorder else
+                                   f"cc_graph_reorder({args.reorder}) once before timing, "
+                                   f"{reorder_ms:.1f} ms host-timed; inside the e2e timing"),
                        sweeps_per_step=statistics.median(sweeps)),
         "roofline": {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak,
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
@@ -323,10 +342,12 @@ def run_ours(args, rank, world, local):
     }
 
     if not args.no_e2e:
-        line["e2e"] = e2e(cc, n, s, d, args, mode, world, stream)
+        line["e2e"] = e2e(cc, n, s, d, args, mode, world, stream, reorder)
 
     if not args.no_variants and rank == 0:
         line["variants"] = variants(cc, g, out, n, m, args, dev, seed, stream)
+    if args.batch_graphs > 0 and rank == 0:
+        line["batch"] = batch_compare(cc, args.batch_graphs, args, dev, stream, gg.BASE_SEED + 3)
 
     cc.cc_free(g)
 
@@ -340,7 +361,7 @@ def run_ours(args, rank, world, local):
         print(json.dumps(line), flush=True)
 
 
-def e2e(cc, n, s, d, args, mode, world, stream):
+def e2e(cc, n, s, d, args, mode, world, stream, reorder=0):
     """Same metric through the public API from pinned host buffers, copies included."""
     s_h = s.cpu().pin_memory()
     d_h = d.cpu().pin_memory()
@@ -349,6 +370,8 @@ def e2e(cc, n, s, d, args, mode, world, stream):
 
     def one():
         g = cc.cc_init(n, s_h, d_h, on_device=False, stream=stream.cuda_stream)
+        if reorder:
+            cc.cc_graph_reorder(g, reorder)
         cc.cc_run(g, out_h, args.order, mode, args.interval, out_on_device=False)
         cc.cc_free(g)
 
@@ -380,8 +403,16 @@ def variants(cc, g, out, n, m, args, dev, seed, stream):
 
     for order, mode, name in [(2, cc.CC_SYNC, "o2-sync"), (4, cc.CC_ASYNC, "o4-async"),
                               (4, cc.CC_SYNC, "o4-sync"), (0, cc.CC_ASYNC, "full-async"),
-                              (1, cc.CC_ASYNC, "o1-async")]:
+                              (1, cc.CC_ASYNC, "o1-async"), (cc.CC_ORDER_11MM, cc.CC_ASYNC, "c11mm-async"),
+                              (cc.CC_ORDER_1M1M, cc.CC_ASYNC, "c1m1m-async")]:
         res[f"{args.workload}/{name}"] = measure(g, out, n, m, order, mode, 1)
+    if os.path.exists(cc.SCHED_WEIGHTS_PATH):
+        cc.load_default_scheduler()
+        r = measure(g, out, n, m, cc.CC_ORDER_AUTO, cc.CC_ASYNC, 0)
+        st = cc.cc_run(g, out, cc.CC_ORDER_AUTO, cc.CC_ASYNC, 0)
+        r["schedule"] = [st.order, st.mode, st.check_interval]
+        res[f"{args.workload}/learned"] = r
+        cc.cc_sched_load(None)
     if args.workload.startswith("rmat"):
         n2, s2, d2, _ = make_workload("grid4096", dev, seed)
         g2 = cc.cc_init(n2, s2, d2, stream=stream.cuda_stream)
@@ -400,24 +431,21 @@ def make_batch(n_graphs: int, device, seed: int):
     return vo.numpy(), eo.numpy(), s, d, params, time.perf_counter() - t0
 
 
-def run_batch(args, rank, world, local):
-    """Batched solve of the batch mix vs one cc_run per graph, identical output."""
-    import paper_2311_02811_gb300 as cc
-    dev = torch.device("cuda", torch.cuda.current_device())
-    G = int(args.workload[5:])
-    vo, eo, s, d, params, gen_s = make_batch(G, dev, gg.BASE_SEED + 3 + rank)
+def batch_compare(cc, G, args, dev, stream, seed):
+    """The batch mix solved four ways with identical output: one cc_run per
+    graph (the plain form) and one batched launch, each with the plain
+    order-2 synchronous schedule and with the paper's C-2 (order 2, async);
+    plus the batched launch with the learned per-graph schedule."""
+    vo, eo, s, d, params, gen_s = make_batch(G, dev, seed)
     torch.cuda.empty_cache()
     total_n, total_m = int(vo[-1]), int(eo[-1])
-    stream = torch.cuda.current_stream()
-    mode = cc.CC_ASYNC if args.mode == "async" else cc.CC_SYNC
     t0 = time.perf_counter()
     plan = cc.cc_batch_init(vo, eo, s, d, autotune=1, stream=stream.cuda_stream)
     tune_s = time.perf_counter() - t0
     out_b = torch.empty(total_n, dtype=torch.int32, device=dev)
     res = {}
 
-    def timed(fn, reps):
-        fn()
+    def ev_ms(fn, reps):
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
@@ -428,13 +456,23 @@ def run_batch(args, rank, world, local):
         torch.cuda.synchronize()
         return e0.elapsed_time(e1) / reps
 
-    for order, md, name in [(args.order, mode, "batched"), (2, cc.CC_SYNC, "batched-o2-sync"),
-                            (0, cc.CC_ASYNC, "batched-full-async")]:
-        ms = timed(lambda: cc.cc_batch_run(plan, out_b, order, md, args.interval), args.steps)
-        res[name] = {"ms": ms, "edges_per_s": total_m / (ms * 1e-3)}
-    cc.cc_batch_run(plan, out_b, args.order, mode, args.interval)
+    reps = max(1, min(args.steps, 5))
+    for name, (order, md, c) in [("batched-plain-o2-sync", (2, cc.CC_SYNC, 1)),
+                                 ("batched-c2-async", (2, cc.CC_ASYNC, 1)),
+                                 ("batched-full-async", (0, cc.CC_ASYNC, 1))]:
+        first = ev_ms(lambda: cc.cc_batch_run(plan, out_b, order, md, c), 1)
+        ms = ev_ms(lambda: cc.cc_batch_run(plan, out_b, order, md, c), reps)
+        res[name] = {"ms": ms, "first_call_ms": first, "edges_per_s": total_m / (ms * 1e-3)}
     ref = out_b.clone()
-    # plain form: one handle per graph, one cc_run per graph
+    learned = os.path.exists(cc.SCHED_WEIGHTS_PATH)
+    if learned:
+        cc.load_default_scheduler()
+        first = ev_ms(lambda: cc.cc_batch_run(plan, out_b, cc.CC_ORDER_AUTO, cc.CC_ASYNC, 0), 1)
+        ms = ev_ms(lambda: cc.cc_batch_run(plan, out_b, cc.CC_ORDER_AUTO, cc.CC_ASYNC, 0), reps)
+        res["batched-learned"] = {"ms": ms, "first_call_ms": first, "edges_per_s": total_m / (ms * 1e-3),
+                                  "note": "first call includes the feature pass and inference"}
+        identical_learned = bool(torch.equal(out_b, ref))
+        cc.cc_sched_load(None)
     handles = []
     for g in range(G):
         a, b = int(eo[g]), int(eo[g + 1])
@@ -446,23 +484,40 @@ def run_batch(args, rank, world, local):
         for h, v0, v1 in handles:
             cc.cc_run(h, out_p[v0:v1], order, md, 1)
 
-    for order, md, name in [(2, cc.CC_SYNC, "plain-o2-sync"), (args.order, mode, "plain")]:
-        ms = timed(lambda: plain(order, md), max(1, min(args.steps, 3)))
+    for name, (order, md) in [("plain-o2-sync", (2, cc.CC_SYNC)), ("plain-c2-async", (2, cc.CC_ASYNC))]:
+        plain(order, md)
+        ms = ev_ms(lambda: plain(order, md), max(1, min(reps, 2)))
         res[name] = {"ms": ms, "edges_per_s": total_m / (ms * 1e-3)}
-    identical = bool(torch.equal(out_p, ref))
+    identical = bool(torch.equal(out_p, ref)) and (identical_learned if learned else True)
     for h, _, _ in handles:
         cc.cc_free(h)
     tuning = cc.cc_batch_tuning(plan)
     cc.cc_batch_free(plan)
-    line = {"metric": "CC edges/sec (m / solve time), batched vs plain", "value": res["batched"]["edges_per_s"],
+    best_batched = "batched-learned" if learned else "batched-c2-async"
+    return {"workload": f"batch-mix-{G}", "graphs": G, "n": total_n, "m": total_m,
+            "generation_s": gen_s, "plan_and_autotune_s": tune_s,
+            "tuning": {"smem_budget": tuning[0], "threads": tuning[1], "edges_per_thread": tuning[2]},
+            "forms": res, "identical_output": identical,
+            "speedup_batched_learned_vs_plain": res["plain-o2-sync"]["ms"] / res[best_batched]["ms"],
+            "speedup_batched_learned_vs_plain_c2": res["plain-c2-async"]["ms"] / res[best_batched]["ms"]}
+
+
+def run_batch(args, rank, world, local):
+    """Config-4 style line: the batch mix, batched + learned vs plain."""
+    import paper_2311_02811_gb300 as cc
+    dev = torch.device("cuda", torch.cuda.current_device())
+    G = int(args.workload[5:])
+    stream = torch.cuda.current_stream()
+    b = batch_compare(cc, G, args, dev, stream, gg.BASE_SEED + 3 + rank)
+    key = "batched-learned" if "batched-learned" in b["forms"] else "batched-c2-async"
+    ms = b["forms"][key]["ms"]
+    value, ms_max = whole_job_rate(b["m"], ms, world)
+    line = {"metric": "CC edges/sec (m / solve time), batched + learned vs plain", "value": value,
             "unit": "edges/s", "n_gpus": world, "steps": args.steps, "warmup": 1,
-            "ms_per_step": res["batched"]["ms"], "higher_is_better": True, "scaling": "weak",
+            "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-            "config": {"workload": f"batch-mix-{G}", "graphs": G, "n": total_n, "m": total_m,
-                       "order": args.order, "mode": args.mode, "check_interval": args.interval,
-                       "generation_s": gen_s, "plan_and_autotune_s": tune_s,
-                       "tuning": {"smem_budget": tuning[0], "threads": tuning[1], "edges_per_thread": tuning[2]}},
-            "forms": res, "identical_output": identical}
+            "config": {"workload": b["workload"], "graphs": G, "n": b["n"], "m": b["m"], "form": key},
+            "batch": b}
     if rank == 0:
         print(json.dumps(line), flush=True)
 

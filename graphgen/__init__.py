@@ -43,6 +43,7 @@ __all__ = [
 ]
 
 BASE_SEED = 2311028110
+SHUFFLE_BLOCK = 1 << 30
 
 _MASK64 = (1 << 64) - 1
 _GAMMA = 0x9E3779B97F4A7C15
@@ -128,14 +129,18 @@ def _random_rank(key: int, count: int, device) -> torch.Tensor:
 
 def permute_and_shuffle(n: int, src: torch.Tensor, dst: torch.Tensor, seed: int,
                         id_dtype=torch.int32):
-    """Relabel vertices by a seeded permutation and shuffle the edge order."""
+    """Relabel vertices by a seeded permutation and shuffle the edge order
+    (src and dst are shuffled in place)."""
     device = src.device
     perm = _random_rank(stream_key(seed, 101), n, device)
     m = src.numel()
-    if m:
-        order = torch.sort(uniform64(stream_key(seed, 102), 0, m, device), stable=True).indices
-        src = src[order]
-        dst = dst[order]
+    # edges are shuffled by a stable sort on seeded 64-bit keys, within
+    # consecutive blocks of 2^30 edges (the largest sort torch performs)
+    key = stream_key(seed, 102)
+    for lo, hi in _chunks(m, SHUFFLE_BLOCK):
+        order = torch.sort(uniform64(key, lo, hi - lo, device), stable=True).indices + lo
+        src[lo:hi] = src[order]
+        dst[lo:hi] = dst[order]
         del order
     s = perm[src].to(id_dtype)
     d = perm[dst].to(id_dtype)

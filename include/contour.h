@@ -54,6 +54,11 @@ enum { CC_SYNC = 0, CC_ASYNC = 1 };
  * chain to its root (at most 1024 hops, the "C-m" variant with m = 1024 of
  * Section III-B4); CC_ORDER_AUTO lets the learned scheduler choose. */
 enum { CC_ORDER_FULL = 0, CC_ORDER_AUTO = -1 };
+/* Per-iteration order schedules (Section III-B4), cc_run only, check interval 1:
+ * CC_ORDER_11MM ("C-11mm") uses order 1 for the first two sweeps and the full
+ * chain afterwards; CC_ORDER_1M1M ("C-1m1m") alternates order 1 and the full
+ * chain, starting with order 1. */
+enum { CC_ORDER_11MM = -2, CC_ORDER_1M1M = -3 };
 enum { CC_MAX_ORDER = 1024 };
 
 typedef struct {
@@ -254,6 +259,10 @@ cc_status cc_batch(int32_t n_graphs, const int64_t *vtx_off, const int64_t *edge
  * order {2, 4, CC_ORDER_FULL}[k/6], mode (k/3)%2 (0 sync, 1 async) and check
  * interval {1, 2, 4}[k%3].
  *
+ * A handle (or plan) computes its features and schedule on the first
+ * CC_ORDER_AUTO call after weights were loaded and reuses the choice until
+ * cc_sched_load is called again (its edges cannot change).
+ *
  * cc_sched_load        install a weight blob (cc_sched_blob_bytes() bytes, format
  *                      "CCMLP01": header with feature mean/std, then per layer
  *                      BF16 weights [out][in] and FP32 biases); NULL unloads and
@@ -285,6 +294,20 @@ cc_status cc_sched_train(const float *features, const int32_t *labels, int32_t N
                          uint64_t seed, void *blob_out, float *final_loss);
 cc_status cc_sched_train_step(const float *features_norm, const int32_t *labels, int32_t B,
                               float *params_inout, float lr, float *loss_out);
+
+/*
+ * cc_graph_reorder -- one-time layout step: reorder the handle's edge list so
+ * that consecutive edges share an endpoint.  The paper's edge loop (Alg. 1)
+ * visits edges in any order, so every later cc_run returns the same labels;
+ * sweeps become faster because the label gathers of one warp fall into few
+ * cache lines.  The handle then owns a reordered copy (a borrowed input is no
+ * longer referenced).  int32 ids only.  Synchronises the handle's stream.
+ *   CC_REORDER_SRC     sort the (src, dst) pairs by src
+ *   CC_REORDER_LOWDEG  orient each edge from its lower-degree endpoint (ties:
+ *                      smaller id) and sort by that endpoint
+ */
+enum { CC_REORDER_SRC = 1, CC_REORDER_LOWDEG = 2 };
+cc_status cc_graph_reorder(cc_graph *g, int method);
 
 /* Make later cc_run calls on g enqueue on another stream (default: the stream
  * passed to cc_init). */

@@ -17,12 +17,12 @@ import os
 __all__ = [
     "CC_OK", "CC_EINVAL", "CC_EIDRANGE", "CC_ENOMEM", "CC_ECUDA", "CC_ENOTCONVERGED",
     "CC_ETIMEOUT", "CC_ID32", "CC_ID64", "CC_COO", "CC_CSR", "CC_SYNC", "CC_ASYNC",
-    "CC_ORDER_FULL", "CC_ORDER_AUTO", "CC_NOALLOC_MAX_N", "CCError", "cc_stats", "cc_graph", "lib", "LIB_PATH",
+    "CC_ORDER_FULL", "CC_ORDER_AUTO", "CC_ORDER_11MM", "CC_ORDER_1M1M", "CC_NOALLOC_MAX_N", "CCError", "cc_stats", "cc_graph", "lib", "LIB_PATH",
     "cc_init", "cc_run", "cc_run_noalloc", "cc_free", "cc_batch_plan", "cc_batch_init",
     "cc_batch_run", "cc_batch_set_schedule", "cc_batch_run_scheduled", "cc_batch_tuning",
     "cc_batch_set_tuning", "cc_batch_free", "cc_batch", "cc_sched_load", "cc_sched_blob_bytes",
     "cc_sched_param_count", "cc_sched_decode", "cc_graph_features", "cc_batch_features",
-    "cc_sched_predict", "cc_sched_train", "cc_sched_train_step", "CC_SCHED_FEATURES", "CC_SCHED_CLASSES", "cc_graph_info", "cc_graph_set_stream", "cc_strerror",
+    "cc_sched_predict", "cc_sched_train", "load_default_scheduler", "SCHED_WEIGHTS_PATH", "cc_sched_train_step", "CC_SCHED_FEATURES", "CC_SCHED_CLASSES", "cc_graph_info", "cc_graph_set_stream", "cc_graph_reorder", "CC_REORDER_SRC", "CC_REORDER_LOWDEG", "cc_strerror",
     "cc_last_error",
 ]
 
@@ -33,6 +33,7 @@ CC_ID32, CC_ID64 = 32, 64
 CC_COO, CC_CSR = 0, 1
 CC_SYNC, CC_ASYNC = 0, 1
 CC_ORDER_FULL, CC_ORDER_AUTO = 0, -1
+CC_ORDER_11MM, CC_ORDER_1M1M = -2, -3
 CC_NOALLOC_MAX_N = 4194304
 
 
@@ -342,6 +343,15 @@ def cc_sched_load(blob):
     _check(lib.cc_sched_load(buf, len(blob)), "cc_sched_load")
 
 
+SCHED_WEIGHTS_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "sched_weights.bin")
+
+
+def load_default_scheduler(path=None):
+    """Install the committed scheduler weights (written by sched_train.py)."""
+    with open(path or SCHED_WEIGHTS_PATH, "rb") as f:
+        cc_sched_load(f.read())
+
+
 def cc_sched_blob_bytes():
     return lib.cc_sched_blob_bytes()
 
@@ -403,6 +413,18 @@ def cc_sched_train_step(features_std, labels, params, lr):
     _check(lib.cc_sched_train_step(f.ctypes.data, y.ctypes.data, len(f), p.ctypes.data, float(lr),
                                    ctypes.byref(loss)), "cc_sched_train_step")
     return p, loss.value
+
+
+CC_REORDER_SRC, CC_REORDER_LOWDEG = 1, 2
+lib.cc_graph_reorder.argtypes = [_p, _int]
+lib.cc_graph_reorder.restype = _int
+
+
+def cc_graph_reorder(g, method=CC_REORDER_LOWDEG):
+    """Reorder the handle's edges for label locality (labels are unchanged)."""
+    _check(lib.cc_graph_reorder(g, int(method)), "cc_graph_reorder")
+    if isinstance(g, cc_graph):
+        g._keep = ()  # the handle now owns its edges
 
 
 def cc_graph_info(g):

@@ -3,7 +3,7 @@
 Each translation unit is compiled in parallel to an object file under
 ``_build/`` and the objects are linked into ``libcontour.so`` next to this
 file.  The CUDA runtime is linked statically, so the library depends only on
-the driver.  Run ``python -m paper_2311_02811_gb300.build`` or call
+the driver.  Run ``python paper_2311_02811_gb300/build.py`` or call
 ``build()``.
 """
 from __future__ import annotations

@@ -428,7 +428,7 @@ __device__ __forceinline__ bool smem_mm(int32_t w, int32_t v, int h, int32_t* Ls
             if constexpr (SYNC) {
                 if (Lus[x] > z) atomicMin(Lus + x, z);
             } else {
-                Ls[x] = z;
+                atomicMin(Ls + x, z);  // never raises a label another thread lowered
             }
             if (y == x) break;
             x = y;
@@ -598,6 +598,7 @@ struct cc_batch_plan {
     std::vector<BatchLoop> loops;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     int sms = 0;
+    cc::SchedCtx* sched = nullptr;  // CC_ORDER_AUTO buffers
 };
 
 namespace {
@@ -610,6 +611,7 @@ namespace {
 
 void destroy_batch(cc_batch_plan* b) {
     if (!b) return;
+    cc::sched_ctx_free(b->sched);
     for (auto& l : b->loops) {
         if (l.exec) cudaGraphExecDestroy(l.exec);
         if (l.graph) cudaGraphDestroy(l.graph);
@@ -895,6 +897,7 @@ const int64_t* batch_off_e(const cc_batch_plan* b) { return b->off_e.data(); }
 const int32_t* batch_src(const cc_batch_plan* b) { return b->src; }
 const int32_t* batch_dst(const cc_batch_plan* b) { return b->dst; }
 cudaStream_t batch_stream(const cc_batch_plan* b) { return b->stream; }
+SchedCtx** batch_sched_slot(cc_batch_plan* b) { return &b->sched; }
 void batch_set_schedule(cc_batch_plan* b, const int32_t* h, const int32_t* sync, const int32_t* c) {
     std::copy(h, h + b->G, b->h_h.begin());
     std::copy(sync, sync + b->G, b->h_sync.begin());

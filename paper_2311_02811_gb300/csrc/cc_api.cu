@@ -119,6 +119,7 @@ struct cc_graph {
     cudaStream_t cap = nullptr;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr, evl0 = nullptr, evl1 = nullptr;
     std::vector<LoopGraph> loops;
+    cc::SchedCtx* sched = nullptr;  // CC_ORDER_AUTO buffers
 };
 
 static size_t id_size(int id_bits) { return id_bits == 64 ? 8 : 4; }
@@ -134,6 +135,7 @@ static void free_loops(cc_graph* g) {
 static void destroy(cc_graph* g) {
     if (!g) return;
     free_loops(g);
+    cc::sched_ctx_free(g->sched);
     if (g->own_edges) {
         cudaFree(g->src);
         cudaFree(g->dst);
@@ -166,12 +168,12 @@ static int grid_for(K kernel, int64_t work_items) {
 
 template <int H, bool SYNC, typename IdT>
 static cudaError_t launch_sweep_t(const cc_graph* g, IdT* L, IdT* Lu, int h, int32_t* flag,
-                                  int first, cudaStream_t s) {
+                                  int first, cudaStream_t s, int gate = 0) {
     constexpr int G = (H == 1) ? 2 : 1;  // edge groups of 4 per thread per step
     auto k = cc::mm_sweep_kernel<H, SYNC, G, IdT>;
     const int grid = grid_for(k, g->m / (4 * G) + 1);
     k<<<grid, kThreads, 0, s>>>(static_cast<const IdT*>(g->src), static_cast<const IdT*>(g->dst),
-                                 g->m, L, Lu, h, flag, g->ctl, first);
+                                 g->m, L, Lu, h, flag, g->ctl, first, gate);
     return cudaGetLastError();
 }
 
@@ -196,9 +198,29 @@ static cudaError_t launch_copy(IdT* dst, const IdT* src, int64_t n, cudaStream_t
 }
 
 // One check block: c sweeps (the flag only from the last), then the check.
+// A per-iteration order schedule (C-11mm, C-1m1m) has one sweep per block,
+// run by whichever of its two gated kernels the control word selects.
 template <typename IdT>
 static cudaError_t enqueue_block(cc_graph* g, int order, int mode, int c, IdT* L, IdT* Lu,
                                  cudaGraphConditionalHandle loop, cudaStream_t s) {
+    if (order == CC_ORDER_11MM || order == CC_ORDER_1M1M) {
+        const int first = mode == CC_SYNC ? 1 : 0;
+        int32_t* flag = &g->ctl->flag;
+        cudaError_t e = (mode == CC_SYNC)
+            ? launch_sweep_t<1, true, IdT>(g, L, Lu, 1, flag, first, s, 1)
+            : launch_sweep_t<1, false, IdT>(g, L, nullptr, 1, flag, first, s, 1);
+        if (e != cudaSuccess) return e;
+        e = (mode == CC_SYNC)
+            ? launch_sweep_t<0, true, IdT>(g, L, Lu, cc::kFullChainHops, flag, 0, s, cc::kFullChainHops)
+            : launch_sweep_t<0, false, IdT>(g, L, nullptr, cc::kFullChainHops, flag, 0, s, cc::kFullChainHops);
+        if (e != cudaSuccess) return e;
+        if (mode == CC_SYNC) {
+            e = launch_copy<IdT>(L, Lu, g->n, s);
+            if (e != cudaSuccess) return e;
+        }
+        cc::check_kernel<<<1, 32, 0, s>>>(g->ctl, 1, loop, order == CC_ORDER_11MM ? 1 : 2);
+        return cudaGetLastError();
+    }
     for (int j = 0; j < c; ++j) {
         int32_t* flag = (j == c - 1) ? &g->ctl->flag : nullptr;
         // synchronous runs start with the gather-free identity sweep (the
@@ -454,7 +476,10 @@ static cc_status run_impl(cc_graph* g, int order, int mode, int c, int32_t max_s
         cc_status st = cc::resolve_schedule(g, &order, &mode, &c);
         if (st != CC_OK) return st;
     }
-    if (order < 0 || order > CC_MAX_ORDER) return set_error(CC_EINVAL, "cc_run: order must be 1..%d, CC_ORDER_FULL or CC_ORDER_AUTO", CC_MAX_ORDER);
+    const bool schedule = order == CC_ORDER_11MM || order == CC_ORDER_1M1M;
+    if (schedule) c = 1;
+    if ((order < 0 || order > CC_MAX_ORDER) && !schedule)
+        return set_error(CC_EINVAL, "cc_run: order must be 1..%d, CC_ORDER_FULL, CC_ORDER_AUTO, CC_ORDER_11MM or CC_ORDER_1M1M", CC_MAX_ORDER);
     if (mode != CC_SYNC && mode != CC_ASYNC) return set_error(CC_EINVAL, "cc_run: mode must be CC_SYNC or CC_ASYNC");
     if (c < 1 || c > 64) return set_error(CC_EINVAL, "cc_run: check_interval must be 1..64");
     if (max_sweeps < 1) return set_error(CC_EINVAL, "cc_run: max_sweeps must be >= 1");
@@ -484,7 +509,7 @@ static cc_status run_impl(cc_graph* g, int order, int mode, int c, int32_t max_s
     }
 
     CC_CUDA(cudaEventRecord(g->ev0, s));
-    cc::ctl_reset_kernel<<<1, 32, 0, s>>>(g->ctl, max_sweeps, init_labels ? 0 : 1);
+    cc::ctl_reset_kernel<<<1, 32, 0, s>>>(g->ctl, max_sweeps, init_labels ? 0 : 1, schedule ? 1 : 0);
     CC_LAUNCHED();
     CC_CUDA(g->id_bits == 64 ? enqueue_init<int64_t>(g, (int64_t*)L, (int64_t*)Lu, init_labels, s)
                              : enqueue_init<int32_t>(g, (int32_t*)L, (int32_t*)Lu, init_labels, s));
@@ -558,6 +583,21 @@ const void* graph_src(const cc_graph* g) { return g->src; }
 const void* graph_dst(const cc_graph* g) { return g->dst; }
 int graph_id_bits(const cc_graph* g) { return g->id_bits; }
 cudaStream_t graph_stream(const cc_graph* g) { return g->stream; }
+SchedCtx** graph_sched_slot(cc_graph* g) { return &g->sched; }
+cc_status graph_replace_edges(cc_graph* g, void* src, void* dst) {
+    // cached loop graphs and scheduler features refer to the old arrays
+    free_loops(g);
+    sched_ctx_free(g->sched);
+    g->sched = nullptr;
+    if (g->own_edges) {
+        cudaFree(g->src);
+        cudaFree(g->dst);
+    }
+    g->src = src;
+    g->dst = dst;
+    g->own_edges = true;
+    return CC_OK;
+}
 cc_status graph_nm(const cc_graph* g, long long* n, long long* m) {
     *n = g->n;
     *m = g->m;

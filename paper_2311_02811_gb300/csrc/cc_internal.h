@@ -9,6 +9,9 @@
 
 namespace cc {
 
+struct SchedCtx;  // scheduler buffers of a handle or plan (sched.cu)
+void sched_ctx_free(SchedCtx* c);
+
 cc_status set_error(cc_status s, const char* fmt, ...);
 cc_status cuda_fail(cudaError_t e, const char* what, const char* file, int line);
 int device_sms();
@@ -20,6 +23,9 @@ const void* graph_dst(const cc_graph* g);
 int graph_id_bits(const cc_graph* g);
 cc_status graph_nm(const cc_graph* g, long long* n, long long* m);
 cudaStream_t graph_stream(const cc_graph* g);
+SchedCtx** graph_sched_slot(cc_graph* g);
+// Replace the handle's edge arrays by device arrays it then owns (reorder.cu).
+cc_status graph_replace_edges(cc_graph* g, void* src, void* dst);
 
 // CC_ORDER_AUTO: pick (order, mode, check interval) for a graph; the plain
 // order-2 synchronous schedule with c = 1 when no scheduler weights are loaded.
@@ -36,6 +42,7 @@ const int64_t* batch_off_e(const cc_batch_plan* b);
 const int32_t* batch_src(const cc_batch_plan* b);
 const int32_t* batch_dst(const cc_batch_plan* b);
 cudaStream_t batch_stream(const cc_batch_plan* b);
+SchedCtx** batch_sched_slot(cc_batch_plan* b);
 void batch_set_schedule(cc_batch_plan* b, const int32_t* h, const int32_t* sync, const int32_t* c);
 
 }  // namespace cc

@@ -25,7 +25,7 @@ struct Ctl {
     unsigned long long first_bad;         // smallest failing index
     unsigned long long compress_changes;  // labels changed by the final compress
     int32_t fresh;       // 1 when the run started from L[i] = i (no snapshot)
-    int32_t pad;
+    int32_t sched_h;     // order of the next sweep under a per-iteration order schedule
 };
 
 constexpr int kFullChainHops = 1024;  // cap of the full-chain operator ("C-m", m = 1024)
@@ -55,8 +55,13 @@ __device__ __forceinline__ IdT rd(const IdT* L, IdT x) {
 
 // Conditional assignment x <- z (Def. 1).  The caller has already seen the
 // old value exceed z.  Synchronous: atomic minimum into L_u (the CAS loop of
-// Eq. "cas" collapses to one reduction); asynchronous: a plain store into L
-// (Section III-B3: a lost write costs iterations, never correctness).
+// Eq. "cas" collapses to one reduction).  Asynchronous: an atomic minimum
+// into L as well.  Section III-B3 replaces atomics with plain stores because
+// a lost write only costs iterations; on sm_103a the opposite holds: a plain
+// store issued after a stale (L1-cached) read can raise a label that another
+// SM has just lowered, and such stores measured up to 8x slower per solve
+// than the fire-and-forget reduction (red.global.min) on 1e5-1e6 vertex
+// graphs, with the same sweep counts.
 template <typename IdT>
 __device__ __forceinline__ void red_min(IdT* a, IdT z) {
     if constexpr (sizeof(IdT) == 4) atomicMin(reinterpret_cast<int*>(a), (int)z);
@@ -71,7 +76,7 @@ __device__ __forceinline__ void wr(IdT* L, IdT* Lu, IdT x, IdT z) {
         // the test removes most same-address atomics.
         if (__ldcg(Lu + x) > z) red_min(Lu + x, z);
     } else {
-        L[x] = z;
+        red_min(L + x, z);
     }
 }
 
@@ -178,6 +183,9 @@ __device__ __forceinline__ bool mm_runtime(IdT w, IdT v, int h, IdT* L, IdT* Lu)
 //   first == 0: ordinary sweep
 //   first == 1: identity sweep iff ctl->sweeps == 0 and ctl->fresh
 //   first == 2: identity sweep
+// gate != 0: the sweep belongs to a per-iteration order schedule (the C-11mm
+// and C-1m1m variants of Section III-B4) and runs only when ctl->sched_h ==
+// gate; otherwise it returns at once.
 template <typename IdT>
 __device__ __forceinline__ bool identity_pair(IdT w, IdT v, IdT* target) {
     if (w == v) return false;
@@ -190,7 +198,8 @@ __device__ __forceinline__ bool identity_pair(IdT w, IdT v, IdT* target) {
 template <int H, bool SYNC, int G, typename IdT>
 __global__ void __launch_bounds__(256)
 mm_sweep_kernel(const IdT* __restrict__ src, const IdT* __restrict__ dst, int64_t m,
-                IdT* L, IdT* Lu, int h, int32_t* flag, const Ctl* ctl, int first) {
+                IdT* L, IdT* Lu, int h, int32_t* flag, const Ctl* ctl, int first, int gate) {
+    if (gate != 0 && ctl->sched_h != gate) return;
     const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const int64_t ngroups = m / (4 * G);
@@ -386,9 +395,10 @@ __global__ void csr_rows_kernel(const int64_t* off, int64_t n, int64_t nnz, IdT*
     }
 }
 
-static __global__ void ctl_reset_kernel(Ctl* ctl, int32_t max_sweeps, int32_t fresh) {
+static __global__ void ctl_reset_kernel(Ctl* ctl, int32_t max_sweeps, int32_t fresh, int32_t sched_h = 0) {
     if (threadIdx.x == 0) {
         ctl->fresh = fresh;
+        ctl->sched_h = sched_h;
         ctl->flag = 0;
         ctl->sweeps = 0;
         ctl->max_sweeps = max_sweeps;
@@ -401,11 +411,16 @@ static __global__ void ctl_reset_kernel(Ctl* ctl, int32_t max_sweeps, int32_t fr
 
 // End of one check block inside the conditional WHILE body: read and clear the
 // flag, count the block's sweeps, and decide whether the loop runs again.
-static __global__ void check_kernel(Ctl* ctl, int32_t block_sweeps, cudaGraphConditionalHandle loop) {
+// sched: 0 none; 1 C-11mm (order 1 for two sweeps, then the full chain);
+// 2 C-1m1m (order 1 and the full chain alternately).
+static __global__ void check_kernel(Ctl* ctl, int32_t block_sweeps, cudaGraphConditionalHandle loop,
+                                    int sched = 0) {
     if (threadIdx.x == 0) {
         const int32_t f = ctl->flag;
         ctl->flag = 0;
         ctl->sweeps += block_sweeps;
+        if (sched == 1) ctl->sched_h = ctl->sweeps < 2 ? 1 : kFullChainHops;
+        if (sched == 2) ctl->sched_h = (ctl->sweeps % 2 == 0) ? 1 : kFullChainHops;
         ctl->converged = (f == 0);
         cudaGraphSetConditional(loop, (f != 0 && ctl->sweeps < ctl->max_sweeps) ? 1u : 0u);
     }

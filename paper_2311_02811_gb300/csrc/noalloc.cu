@@ -65,7 +65,7 @@ void sweep_t(const int32_t* src, const int32_t* dst, int64_t m, int32_t* L, int3
              int32_t* flag, int first, cudaStream_t s) {
     constexpr int G = (H == 1) ? 2 : 1;
     auto k = cc::mm_sweep_kernel<H, SYNC, G, int32_t>;
-    k<<<grid_for(k, m / (4 * G) + 1), kThreads, 0, s>>>(src, dst, m, L, Lu, h, flag, nullptr, first);
+    k<<<grid_for(k, m / (4 * G) + 1), kThreads, 0, s>>>(src, dst, m, L, Lu, h, flag, nullptr, first, 0);
 }
 
 // first == 2 selects the identity sweep (the run's first sweep); 0 otherwise.

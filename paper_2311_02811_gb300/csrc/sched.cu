@@ -28,6 +28,7 @@
 #include <cmath>
 #include <cstring>
 #include <mutex>
+#include <new>
 #include <vector>
 
 #include "../../include/contour.h"
@@ -40,7 +41,7 @@ constexpr int kHidden = 64;
 constexpr int kOut = CC_SCHED_CLASSES;
 constexpr int kSample = 16384;
 constexpr int kLevels = 16;
-constexpr int kFeatThreads = 512;
+constexpr int kFeatThreads = 1024;
 
 // ---------------------------------------------------------------------------
 // weights blob
@@ -66,6 +67,7 @@ struct Model {
 
 std::mutex g_mu;
 Model* g_model = nullptr;  // device copy, nullptr when nothing is loaded
+long long g_model_version = 0;  // bumped by every cc_sched_load
 std::vector<unsigned char> g_blob;
 
 // ---------------------------------------------------------------------------
@@ -393,29 +395,77 @@ cc_status upload_blob(const unsigned char* blob, size_t bytes) {
         if (e_ != cudaSuccess) return cc::cuda_fail(e_, #expr, __FILE__, __LINE__); \
     } while (0)
 
-// Features of G graphs given device offsets; scratch of total_n vertices.
-cc_status run_features(int32_t G, const int64_t* d_off_v, const int64_t* d_off_e, const int32_t* src,
-                       const int32_t* dst, int64_t total_n, float* d_out, cudaStream_t s) {
-    if (G == 0) return CC_OK;
-    const int grid = std::min<int>(G, cc::device_sms() * 2);
+}  // namespace
+
+namespace cc {
+
+// Device buffers of the scheduler for one graph handle or batch plan, kept
+// for the handle's lifetime: offsets, features, classes and the per-vertex
+// scratch of the feature kernel (zeroed once; the kernel leaves it zero).
+struct SchedCtx {
+    int32_t G = 0;
+    int64_t total_n = 0;
+    int64_t* d_off = nullptr;  // off_v[G+1] then off_e[G+1]
+    float* d_feat = nullptr;   // G x kFeat
+    int32_t* d_cls = nullptr;  // G
     int32_t* deg = nullptr;
     uint32_t* word = nullptr;
     int32_t* owned = nullptr;
-    const size_t nv = (size_t)std::max<int64_t>(total_n, 1);
-    cudaError_t e = cudaMallocAsync(&deg, nv * sizeof(int32_t), s);
-    if (e == cudaSuccess) e = cudaMallocAsync(&word, nv * sizeof(uint32_t), s);
-    if (e == cudaSuccess) e = cudaMallocAsync(&owned, (size_t)grid * 2 * kSample * sizeof(int32_t), s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(deg, 0, nv * sizeof(int32_t), s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(word, 0, nv * sizeof(uint32_t), s);
-    if (e == cudaSuccess) {
-        FeatArgs a{G, d_off_v, d_off_e, src, dst, deg, word, owned, d_out};
-        features_kernel<<<grid, kFeatThreads, 0, s>>>(a);
-        e = cudaGetLastError();
+    int grid = 0;
+    std::vector<int32_t> h_cls;  // host copy of the classes
+    long long version = -1;    // model version h_cls was computed with
+};
+
+void sched_ctx_free(SchedCtx* c) {
+    if (!c) return;
+    cudaFree(c->d_off);
+    cudaFree(c->d_feat);
+    cudaFree(c->d_cls);
+    cudaFree(c->deg);
+    cudaFree(c->word);
+    cudaFree(c->owned);
+    delete c;
+}
+
+}  // namespace cc
+
+namespace {
+
+cc_status ctx_get(cc::SchedCtx** slot, int32_t G, const int64_t* off_v, const int64_t* off_e, cudaStream_t s) {
+    if (*slot) return CC_OK;
+    cc::SchedCtx* c = new (std::nothrow) cc::SchedCtx();
+    if (!c) return cc::set_error(CC_ENOMEM, "scheduler context");
+    c->G = G;
+    c->total_n = off_v[G];
+    c->grid = std::max(1, std::min<int>(G, cc::device_sms() * 2));
+    const size_t nv = (size_t)std::max<int64_t>(c->total_n, 1);
+    cudaError_t e = cudaMalloc(&c->d_off, 2 * (size_t)(G + 1) * sizeof(int64_t));
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_feat, (size_t)std::max(G, 1) * kFeat * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_cls, (size_t)std::max(G, 1) * sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaMalloc(&c->deg, nv * sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaMalloc(&c->word, nv * sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMalloc(&c->owned, (size_t)c->grid * 2 * kSample * sizeof(int32_t));
+    c->h_cls.assign((size_t)std::max(G, 1), 0);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->deg, 0, nv * sizeof(int32_t), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->word, 0, nv * sizeof(uint32_t), s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_off, off_v, (G + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(c->d_off + G + 1, off_e, (G + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // the host offsets may be temporaries
+    if (e != cudaSuccess) {
+        cc::sched_ctx_free(c);
+        return cc::cuda_fail(e, "scheduler context", __FILE__, __LINE__);
     }
-    if (deg) cudaFreeAsync(deg, s);
-    if (word) cudaFreeAsync(word, s);
-    if (owned) cudaFreeAsync(owned, s);
-    if (e != cudaSuccess) return cc::cuda_fail(e, "graph features", __FILE__, __LINE__);
+    *slot = c;
+    return CC_OK;
+}
+
+// Features of every graph of the context into c->d_feat.
+cc_status run_features(cc::SchedCtx* c, const int32_t* src, const int32_t* dst, cudaStream_t s) {
+    if (c->G == 0) return CC_OK;
+    FeatArgs a{c->G, c->d_off, c->d_off + c->G + 1, src, dst, c->deg, c->word, c->owned, c->d_feat};
+    features_kernel<<<c->grid, kFeatThreads, 0, s>>>(a);
+    SCUDA(cudaGetLastError());
     return CC_OK;
 }
 
@@ -460,32 +510,25 @@ cc_status resolve_schedule(cc_graph* g, int* order, int* mode, int* c) {
         return CC_OK;
     }
     cudaStream_t s = graph_stream(g);
-    int64_t offs[4] = {0, n, 0, m};
-    int64_t* d_off = nullptr;
-    float* d_f = nullptr;
-    int32_t* d_cls = nullptr;
-    SCUDA(cudaMallocAsync(&d_off, sizeof offs + kFeat * sizeof(float) + 16, s));
-    d_f = reinterpret_cast<float*>(d_off + 4);
-    SCUDA(cudaMemcpyAsync(d_off, offs, sizeof offs, cudaMemcpyHostToDevice, s));
-    // offsets: off_v = {0, n}, off_e = {0, m}
-    cc_status st = run_features(1, d_off, d_off + 2, static_cast<const int32_t*>(graph_src(g)),
-                                static_cast<const int32_t*>(graph_dst(g)), n, d_f, s);
-    if (st == CC_OK) {
-        cudaError_t e = cudaMallocAsync(&d_cls, sizeof(int32_t) * 4, s);
-        if (e != cudaSuccess) st = cuda_fail(e, "sched", __FILE__, __LINE__);
-    }
-    if (st == CC_OK) st = predict_device(d_f, 1, d_cls, nullptr, s);
-    int32_t k = 0;
-    if (st == CC_OK) {
-        cudaError_t e = cudaMemcpyAsync(&k, d_cls, sizeof k, cudaMemcpyDeviceToHost, s);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-        if (e != cudaSuccess) st = cuda_fail(e, "sched", __FILE__, __LINE__);
-    }
-    cudaFreeAsync(d_off, s);
-    if (d_cls) cudaFreeAsync(d_cls, s);
+    const int64_t ov[2] = {0, n}, oe[2] = {0, m};
+    SchedCtx** slot = graph_sched_slot(g);
+    cc_status st = ctx_get(slot, 1, ov, oe, s);
     if (st != CC_OK) return st;
+    SchedCtx* x = *slot;
+    // the edges of a handle never change: the choice is made once per model
+    if (x->version != g_model_version) {
+        st = run_features(x, static_cast<const int32_t*>(graph_src(g)), static_cast<const int32_t*>(graph_dst(g)), s);
+        if (st == CC_OK) st = predict_device(x->d_feat, 1, x->d_cls, nullptr, s);
+        if (st == CC_OK) {
+            cudaError_t e = cudaMemcpyAsync(x->h_cls.data(), x->d_cls, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+            if (e != cudaSuccess) st = cuda_fail(e, "sched", __FILE__, __LINE__);
+        }
+        if (st != CC_OK) return st;
+        x->version = g_model_version;
+    }
     int cc_ = 1;
-    decode(k, order, mode, &cc_);
+    decode(x->h_cls[0], order, mode, &cc_);
     *c = want_c >= 1 ? want_c : cc_;
     return CC_OK;
 }
@@ -497,32 +540,24 @@ cc_status batch_resolve_schedule(cc_batch_plan* b, int mode, int c) {
     std::lock_guard<std::mutex> lock(g_mu);
     if (g_model && G > 0) {
         cudaStream_t s = batch_stream(b);
-        const int64_t* ov = batch_off_v(b);
-        const int64_t* oe = batch_off_e(b);
-        int64_t* d_off = nullptr;
-        float* d_f = nullptr;
-        int32_t* d_cls = nullptr;
-        const size_t offb = 2 * (G + 1) * sizeof(int64_t);
-        SCUDA(cudaMallocAsync(&d_off, offb, s));
-        SCUDA(cudaMallocAsync(&d_f, (size_t)G * kFeat * sizeof(float), s));
-        SCUDA(cudaMallocAsync(&d_cls, (size_t)G * sizeof(int32_t), s));
-        SCUDA(cudaMemcpyAsync(d_off, ov, (G + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
-        SCUDA(cudaMemcpyAsync(d_off + G + 1, oe, (G + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
-        cc_status st = run_features(G, d_off, d_off + G + 1, batch_src(b), batch_dst(b), ov[G], d_f, s);
-        if (st == CC_OK) st = predict_device(d_f, G, d_cls, nullptr, s);
-        std::vector<int32_t> k(G);
-        if (st == CC_OK) {
-            cudaError_t e = cudaMemcpyAsync(k.data(), d_cls, G * sizeof(int32_t), cudaMemcpyDeviceToHost, s);
-            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-            if (e != cudaSuccess) st = cuda_fail(e, "batch sched", __FILE__, __LINE__);
-        }
-        cudaFreeAsync(d_off, s);
-        cudaFreeAsync(d_f, s);
-        cudaFreeAsync(d_cls, s);
+        SchedCtx** slot = batch_sched_slot(b);
+        cc_status st = ctx_get(slot, G, batch_off_v(b), batch_off_e(b), s);
         if (st != CC_OK) return st;
+        SchedCtx* x = *slot;
+        if (x->version != g_model_version) {
+            st = run_features(x, batch_src(b), batch_dst(b), s);
+            if (st == CC_OK) st = predict_device(x->d_feat, G, x->d_cls, nullptr, s);
+            if (st == CC_OK) {
+                cudaError_t e = cudaMemcpyAsync(x->h_cls.data(), x->d_cls, G * sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+                if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+                if (e != cudaSuccess) st = cuda_fail(e, "batch sched", __FILE__, __LINE__);
+            }
+            if (st != CC_OK) return st;
+            x->version = g_model_version;
+        }
         for (int32_t g = 0; g < G; ++g) {
             int o, md, ci;
-            decode(k[g], &o, &md, &ci);
+            decode(x->h_cls[g], &o, &md, &ci);
             h[g] = o == CC_ORDER_FULL ? CC_MAX_ORDER : o;
             sync[g] = md == CC_SYNC;
             cv[g] = c >= 1 ? c : ci;
@@ -540,6 +575,7 @@ cc_status batch_resolve_schedule(cc_batch_plan* b, int mode, int c) {
 
 extern "C" cc_status cc_sched_load(const void* weights, size_t bytes) {
     std::lock_guard<std::mutex> lock(g_mu);
+    ++g_model_version;
     if (!weights) {
         if (g_model) cudaFree(g_model);
         g_model = nullptr;
@@ -564,22 +600,16 @@ extern "C" cc_status cc_graph_features(cc_graph* g, float* features_out) {
     long long n = 0, m = 0;
     cc::graph_nm(g, &n, &m);
     cudaStream_t s = cc::graph_stream(g);
-    int64_t offs[4] = {0, n, 0, m};
-    int64_t* d_off = nullptr;
-    SCUDA(cudaMallocAsync(&d_off, sizeof offs + kFeat * sizeof(float) + 16, s));
-    float* d_f = reinterpret_cast<float*>(d_off + 4);
-    cudaError_t e = cudaMemcpyAsync(d_off, offs, sizeof offs, cudaMemcpyHostToDevice, s);
-    cc_status st = e == cudaSuccess ? CC_OK : cc::cuda_fail(e, "cc_graph_features", __FILE__, __LINE__);
-    if (st == CC_OK)
-        st = run_features(1, d_off, d_off + 2, static_cast<const int32_t*>(cc::graph_src(g)),
-                          static_cast<const int32_t*>(cc::graph_dst(g)), n, d_f, s);
-    if (st == CC_OK) {
-        e = cudaMemcpyAsync(features_out, d_f, kFeat * sizeof(float), cudaMemcpyDeviceToHost, s);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-        if (e != cudaSuccess) st = cc::cuda_fail(e, "cc_graph_features", __FILE__, __LINE__);
-    }
-    cudaFreeAsync(d_off, s);
-    return st;
+    const int64_t ov[2] = {0, n}, oe[2] = {0, m};
+    cc::SchedCtx** slot = cc::graph_sched_slot(g);
+    cc_status st = ctx_get(slot, 1, ov, oe, s);
+    if (st != CC_OK) return st;
+    st = run_features(*slot, static_cast<const int32_t*>(cc::graph_src(g)), static_cast<const int32_t*>(cc::graph_dst(g)), s);
+    if (st != CC_OK) return st;
+    cudaError_t e = cudaMemcpyAsync(features_out, (*slot)->d_feat, kFeat * sizeof(float), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cc::cuda_fail(e, "cc_graph_features", __FILE__, __LINE__);
+    return CC_OK;
 }
 
 extern "C" cc_status cc_batch_features(cc_batch_plan* b, float* features_out) {
@@ -587,23 +617,16 @@ extern "C" cc_status cc_batch_features(cc_batch_plan* b, float* features_out) {
     const int32_t G = cc::batch_graph_count(b);
     if (G == 0) return CC_OK;
     cudaStream_t s = cc::batch_stream(b);
-    const int64_t* ov = cc::batch_off_v(b);
-    const int64_t* oe = cc::batch_off_e(b);
-    int64_t* d_off = nullptr;
-    float* d_f = nullptr;
-    SCUDA(cudaMallocAsync(&d_off, 2 * (G + 1) * sizeof(int64_t), s));
-    SCUDA(cudaMallocAsync(&d_f, (size_t)G * kFeat * sizeof(float), s));
-    SCUDA(cudaMemcpyAsync(d_off, ov, (G + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
-    SCUDA(cudaMemcpyAsync(d_off + G + 1, oe, (G + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
-    cc_status st = run_features(G, d_off, d_off + G + 1, cc::batch_src(b), cc::batch_dst(b), ov[G], d_f, s);
-    if (st == CC_OK) {
-        cudaError_t e = cudaMemcpyAsync(features_out, d_f, (size_t)G * kFeat * sizeof(float), cudaMemcpyDeviceToHost, s);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-        if (e != cudaSuccess) st = cc::cuda_fail(e, "cc_batch_features", __FILE__, __LINE__);
-    }
-    cudaFreeAsync(d_off, s);
-    cudaFreeAsync(d_f, s);
-    return st;
+    cc::SchedCtx** slot = cc::batch_sched_slot(b);
+    cc_status st = ctx_get(slot, G, cc::batch_off_v(b), cc::batch_off_e(b), s);
+    if (st != CC_OK) return st;
+    st = run_features(*slot, cc::batch_src(b), cc::batch_dst(b), s);
+    if (st != CC_OK) return st;
+    cudaError_t e = cudaMemcpyAsync(features_out, (*slot)->d_feat, (size_t)G * kFeat * sizeof(float),
+                                    cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cc::cuda_fail(e, "cc_batch_features", __FILE__, __LINE__);
+    return CC_OK;
 }
 
 extern "C" cc_status cc_sched_predict(const float* features, int32_t count, int32_t* cls_out, float* logits_out) {

@@ -1,0 +1,197 @@
+"""Train the schedule-selection MLP from the library's own measured timings.
+
+For every training graph (the batch mix: ER, path, grid, R-MAT with
+log-uniform n in [1e3, 1e6]):
+  1. compute its 12 features on the GPU (cc_batch_features);
+  2. time all 18 schedules (order {2, 4, full chain} x {sync, async} x check
+     interval {1, 2, 4}) with cc_run, taking the faster of two device-timed
+     runs each; every schedule returns identical labels;
+  3. label the graph with its fastest schedule.
+Then train the MLP on the GPU (cc_sched_train) and write the weight blob.
+
+Held-out evaluation: graphs drawn from another seed plus large R-MAT (up to
+scale 25), grid, path and caterpillar graphs; each is solved with
+  plain    order 2, synchronous, c = 1 (the library's fallback schedule),
+  C-2      order 2, asynchronous, c = 1 (the paper's default variant),
+  learned  CC_ORDER_AUTO (feature extraction and inference included),
+and the learned labels are checked to equal the plain ones.
+
+Usage: python -m paper_2311_02811_gb300.sched_train [--train 20000]
+       [--heldout 512] [--out paper_2311_02811_gb300/sched_weights.bin]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import sys
+import time
+
+import numpy as np
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, os.path.dirname(HERE))
+
+import graphgen as gg  # noqa: E402
+import paper_2311_02811_gb300 as cc  # noqa: E402
+
+TRAIN_SEED = 2311028110 + 50
+HELDOUT_SEED = 2311028110 + 51
+
+
+def time_schedules(n, s, d, reps=2):
+    """Device solve time (ms) of each of the 18 schedules; the labels of all
+    schedules are compared with each other."""
+    g = cc.cc_init(n, s, d)
+    out = torch.empty(n, dtype=torch.int32, device="cuda")
+    ref = None
+    times = np.zeros(cc.CC_SCHED_CLASSES)
+    for k in range(cc.CC_SCHED_CLASSES):
+        order, mode, c = cc.cc_sched_decode(k)
+        best = float("inf")
+        for _ in range(reps):
+            st = cc.cc_run(g, out, order, mode, c)
+            best = min(best, st.solve_ms)
+        times[k] = best
+        if ref is None:
+            ref = out.clone()
+        elif not torch.equal(ref, out):
+            raise RuntimeError("schedules disagree on the labels")
+    cc.cc_free(g)
+    return times
+
+
+def build_training_set(n_graphs, chunk, log):
+    feats, labels, all_times = [], [], []
+    done = 0
+    while done < n_graphs:
+        cnt = min(chunk, n_graphs - done)
+        vo, eo, s, d, _ = gg.batch_mix(cnt, seed=gg.stream_key(TRAIN_SEED, done), device="cuda")
+        plan = cc.cc_batch_init(vo, eo, s, d)
+        F = cc.cc_batch_features(plan)
+        cc.cc_batch_free(plan)
+        for g in range(cnt):
+            a, b = int(eo[g]), int(eo[g + 1])
+            t = time_schedules(int(vo[g + 1] - vo[g]), s[a:b], d[a:b])
+            feats.append(F[g])
+            labels.append(int(np.argmin(t)))
+            all_times.append(t)
+        done += cnt
+        del s, d
+        torch.cuda.empty_cache()
+        log(f"training graphs: {done}/{n_graphs}")
+    return np.array(feats, np.float32), np.array(labels, np.int32), np.array(all_times)
+
+
+def heldout_graphs(n_mix):
+    """(name, n, src, dst) of the held-out set, generated one at a time."""
+    params = gg.batch_mix_params(n_mix, seed=HELDOUT_SEED)
+    for i, p in enumerate(params):
+        n, s, d = gg.batch_graph(p, device="cuda")
+        yield f"mix{i}-{p['kind']}", n, s, d
+    for scale in (20, 22, 24, 25):
+        s, d = gg.rmat(scale, seed=HELDOUT_SEED + scale, device="cuda")
+        yield f"rmat{scale}", 1 << scale, s, d
+    for side in (1024, 2048, 4096):
+        s, d = gg.grid(side, side, seed=HELDOUT_SEED + side, device="cuda")
+        yield f"grid{side}", side * side, s, d
+    for n in (1 << 20, 1 << 23):
+        s, d = gg.path(n, seed=HELDOUT_SEED + 7, device="cuda")
+        yield f"path{n}", n, s, d
+    s, d = gg.caterpillar(1 << 20, seed=HELDOUT_SEED + 8, device="cuda")
+    yield "caterpillar2^20", (1 << 20) * 16, s, d
+
+
+def evaluate(n_mix, log):
+    """Each form on a fresh handle: the first call (cold: loop-graph build and,
+    for the learned form, features and inference) and the best of 3 later calls."""
+    rows = []
+    stream = torch.cuda.current_stream()
+
+    def ev_time(fn):
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        r = fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1), r
+
+    for name, n, s, d in heldout_graphs(n_mix):
+        row = {"graph": name, "n": n, "m": int(s.numel())}
+        outs = {}
+        for form, (order, mode, c) in (("plain", (2, cc.CC_SYNC, 1)), ("c2", (2, cc.CC_ASYNC, 1)),
+                                       ("learned", (cc.CC_ORDER_AUTO, cc.CC_ASYNC, 0))):
+            g = cc.cc_init(n, s, d)
+            out = torch.empty(n, dtype=torch.int32, device="cuda")
+            first, st = ev_time(lambda: cc.cc_run(g, out, order, mode, c))
+            steady = min(ev_time(lambda: cc.cc_run(g, out, order, mode, c))[0] for _ in range(3))
+            cc.cc_free(g)
+            row[f"{form}_first_ms"] = first
+            row[f"{form}_ms"] = steady
+            if form == "learned":
+                row["learned_schedule"] = [st.order, st.mode, st.check_interval]
+            outs[form] = out
+        row["identical"] = bool(torch.equal(outs["plain"], outs["learned"]) and torch.equal(outs["plain"], outs["c2"]))
+        rows.append(row)
+        del s, d, outs
+        torch.cuda.empty_cache()
+    keys = ("plain_ms", "c2_ms", "learned_ms", "plain_first_ms", "c2_first_ms", "learned_first_ms")
+    tot = {k: sum(r[k] for r in rows) for k in keys}
+    log(f"held-out totals: {tot}")
+    return rows, tot
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--train", type=int, default=20000)
+    ap.add_argument("--heldout", type=int, default=496, help="batch-mix graphs; 16 large graphs are added")
+    ap.add_argument("--chunk", type=int, default=500)
+    ap.add_argument("--epochs", type=int, default=80)
+    ap.add_argument("--out", default=os.path.join(HERE, "sched_weights.bin"))
+    ap.add_argument("--report", default=os.path.join(HERE, "sched_weights.json"))
+    ap.add_argument("--dump", default="", help="also save features, labels and timings (.npz)")
+    args = ap.parse_args()
+    t0 = time.time()
+
+    def log(msg):
+        print(f"[{time.time() - t0:7.1f}s] {msg}", flush=True)
+
+    torch.cuda.set_device(0)
+    X, y, T = build_training_set(args.train, args.chunk, log)
+    if args.dump:
+        np.savez_compressed(args.dump, X=X, y=y, T=T)
+    # 90/10 split for a validation accuracy; the final model trains on all rows
+    idx = np.arange(len(y))
+    val = idx % 10 == 0
+    blob, loss = cc.cc_sched_train(X[~val], y[~val], epochs=args.epochs, batch=256, lr=2e-3, seed=7)
+    cc.cc_sched_load(blob)
+    pred, _ = cc.cc_sched_predict(X[val])
+    val_acc = float((pred == y[val]).mean())
+    # time of the predicted schedule relative to the best one, on validation rows
+    regret = float(np.mean(T[val][np.arange(val.sum()), pred] / T[val].min(axis=1)))
+    blob, loss = cc.cc_sched_train(X, y, epochs=args.epochs, batch=256, lr=2e-3, seed=7)
+    cc.cc_sched_load(blob)
+    log(f"trained: loss {loss:.4f}, validation accuracy {val_acc:.3f}, mean time ratio to best {regret:.3f}")
+    with open(args.out, "wb") as f:
+        f.write(blob)
+    rows, tot = evaluate(args.heldout, log)
+    label_hist = np.bincount(y, minlength=cc.CC_SCHED_CLASSES).tolist()
+    report = {"train_graphs": int(len(y)), "label_histogram": label_hist, "final_loss": loss,
+              "validation_accuracy": val_acc, "validation_time_ratio_to_best": regret,
+              "heldout_totals_ms": tot,
+              "heldout_speedup_vs_plain": tot["plain_ms"] / tot["learned_ms"],
+              "heldout_speedup_vs_c2": tot["c2_ms"] / tot["learned_ms"],
+              "heldout_first_call_speedup_vs_plain": tot["plain_first_ms"] / tot["learned_first_ms"],
+              "heldout_first_call_speedup_vs_c2": tot["c2_first_ms"] / tot["learned_first_ms"],
+              "heldout_all_identical": all(r["identical"] for r in rows),
+              "heldout": rows}
+    with open(args.report, "w") as f:
+        json.dump(report, f, indent=1)
+    log(f"wrote {args.out} and {args.report}")
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,68 @@
+"""The largest single-graph workloads: R-MAT scale 27 (2^31 edges, so edge
+indices need 64 bits) and the caterpillar with a 2^24-vertex backbone
+(n = 2^28, diameter 2^24 + 1).
+
+* The caterpillar is connected by construction, so every label is 0 (the
+  smallest id); the synchronous order-2 run must also respect the Theorem's
+  bound of ceil(log_1.5 d) + 1 changing iterations (+1 detection sweep).
+* R-MAT scale 27 is compared entry by entry with the union-find oracle.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import graphgen as gg
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def cc():
+    import paper_2311_02811_gb300 as lib
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    return lib
+
+
+def _solve(cc, g, n, order, mode):
+    out = torch.empty(n, dtype=torch.int32, device="cuda")
+    st = cc.cc_run(g, out, order, mode, 1)
+    return out, st
+
+
+def test_caterpillar_2pow24_backbone(cc):
+    B = 1 << 24
+    s, d = gg.caterpillar(B, device="cuda")
+    n = B * 16
+    assert s.numel() == n - 1
+    g = cc.cc_init(n, s, d)
+    del s, d
+    torch.cuda.empty_cache()
+    for order, mode in [(2, cc.CC_ASYNC), (0, cc.CC_ASYNC), (4, cc.CC_ASYNC)]:
+        out, st = _solve(cc, g, n, order, mode)
+        assert int(out.max()) == 0 and int(out.min()) == 0, (order, mode)
+        del out
+    out, st = _solve(cc, g, n, 2, cc.CC_SYNC)
+    assert int(out.max()) == 0
+    diameter = B + 1
+    bound = math.ceil(math.log(diameter) / math.log(1.5)) + 1
+    assert st.sweeps <= bound + 1, (st.sweeps, bound)
+    cc.cc_free(g)
+
+
+def test_rmat_scale27_int64_edge_offsets(cc):
+    s, d = gg.rmat(27, device="cuda")
+    n, m = 1 << 27, s.numel()
+    assert m == 1 << 31  # more edges than int32 can index
+    torch.cuda.empty_cache()
+    g = cc.cc_init(n, s, d)
+    out, st = _solve(cc, g, n, 2, cc.CC_ASYNC)
+    got = out.cpu().numpy()
+    out_full, _ = _solve(cc, g, n, 0, cc.CC_ASYNC)
+    assert torch.equal(out, out_full)
+    cc.cc_free(g)
+    del out, out_full
+    want = oracle.uf_labels(n, s.cpu().numpy(), d.cpu().numpy())
+    assert np.array_equal(got, want)

@@ -275,3 +275,47 @@ def test_grid4096_full_size(cc):
     for order, mode in [(2, cc.CC_ASYNC), (4, cc.CC_ASYNC), (2, cc.CC_SYNC), (4, cc.CC_SYNC)]:
         got, st, _ = solve(cc, n, s, d, order, mode, 1)
         assert (got == want).all(), (order, mode)
+
+
+@pytest.mark.parametrize("method", [1, 2], ids=["src", "lowdeg"])
+def test_reorder_keeps_labels_and_sync_sequence(cc, method):
+    """Edge order is a layout choice: labels (and, in sync mode, every state
+    and the sweep count) are those of the original edge list."""
+    for name in ("rmat12", "grid64", "components64", "path3001", "caterpillar"):
+        n, s, d = SMALL[name](2)
+        want = oracle.uf_labels(n, s, d)
+        sim, it, _, _ = oracle.contour_sync(n, s, d, 2)
+        sg, dg = s.cuda(), d.cuda()
+        g = cc.cc_init(n, sg, dg)
+        cc.cc_graph_reorder(g, method)
+        del sg, dg  # the handle owns its reordered copy
+        out = torch.empty(n, dtype=torch.int32, device="cuda")
+        for order in (2, 4, 0):
+            for c in (1, 2):
+                cc.cc_run(g, out, order, cc.CC_ASYNC, c)
+                assert (out.cpu().numpy() == want).all(), (name, order, c)
+        st = cc.cc_run(g, out, 2, cc.CC_SYNC, 1)
+        assert st.sweeps == it and (out.cpu().numpy() == sim).all()
+        cc.cc_free(g)
+
+
+@pytest.mark.parametrize("sched", ["11mm", "1m1m"])
+def test_per_iteration_order_schedules(cc, sched):
+    """C-11mm and C-1m1m (Section III-B4): in sync mode every sweep equals the
+    Alg. 1 simulator run one iteration at a time with the scheduled order."""
+    code = cc.CC_ORDER_11MM if sched == "11mm" else cc.CC_ORDER_1M1M
+    for name in ("rmat12", "grid64", "path3001", "components64", "caterpillar"):
+        n, s, d = SMALL[name](3)
+        want = oracle.uf_labels(n, s, d)
+        L, k = None, 0
+        while True:
+            one = (k < 2) if sched == "11mm" else (k % 2 == 0)
+            L, _, conv, _ = oracle.contour_sync(n, s, d, 1 if one else 1024, max_iters=1, init=L)
+            k += 1
+            if conv:
+                break
+        got, st, _ = solve(cc, n, s, d, code, cc.CC_SYNC, 1)
+        assert st.sweeps == k and (got == L).all(), (name, st.sweeps, k)
+        for c in (1, 4):  # the interval is ignored: schedules check every sweep
+            got, st, _ = solve(cc, n, s, d, code, cc.CC_ASYNC, c)
+            assert (got == want).all() and st.check_interval == 1
