@@ -49,7 +49,7 @@ def parse():
     p.add_argument("--cpu-seconds", type=float, default=12.0)
     p.add_argument("--batch-graphs", type=int, default=1024,
                    help="also compare batched + learned vs plain on a batch-mix of this many graphs (0: off)")
-    p.add_argument("--reorder", choices=["none", "src", "lowdeg"], default="none",
+    p.add_argument("--reorder", choices=["none", "src", "lowdeg"], default="lowdeg",
                    help="cc_graph_reorder layout step once before timing (included in e2e)")
     p.add_argument("--entry", choices=["cc_run", "noalloc"], default="cc_run",
                    help="cc_run (conditional CUDA-graph loop) or cc_run_noalloc (host-polled "
@@ -268,9 +268,9 @@ def timed_runs(cc, g, out, n_steps, order, mode, interval, stream, edges=None):
         if edges is None:
             stats.append(cc.cc_run(g, out, order, mode, interval))
         else:
-            n, s, d = edges
+            n, s, d, m = edges
             stats.append(_NoallocStats(cc.cc_run_noalloc(n, s, d, out, order, mode, interval,
-                                                         stream=stream.cuda_stream)))
+                                                         stream=stream.cuda_stream, m=m)))
     ev1.record(stream)
     torch.cuda.synchronize()
     return ev0.elapsed_time(ev1), stats
@@ -294,7 +294,9 @@ def run_ours(args, rank, world, local):
         cc.cc_graph_reorder(g, reorder)
         reorder_ms = 1e3 * (time.perf_counter() - t0)
     out = torch.empty(n, dtype=torch.int32, device=dev)
-    edges = (n, s, d) if args.entry == "noalloc" else None
+    # the no-alloc entry runs the same sweep kernel on the handle's (possibly
+    # reordered) edge arrays with host-polled plain launches
+    edges = (n, *cc.cc_graph_edges(g), m) if args.entry == "noalloc" else None
     timed_runs(cc, g, out, args.warmup, args.order, mode, args.interval, stream, edges)
 
     sampler = ClockSampler(local)
@@ -343,6 +345,8 @@ def run_ours(args, rank, world, local):
 
     if not args.no_e2e:
         line["e2e"] = e2e(cc, n, s, d, args, mode, world, stream, reorder)
+        if reorder:
+            line["e2e_without_reorder"] = e2e(cc, n, s, d, args, mode, world, stream, 0)
 
     if not args.no_variants and rank == 0:
         line["variants"] = variants(cc, g, out, n, m, args, dev, seed, stream)

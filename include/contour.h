@@ -207,7 +207,9 @@ cc_status cc_run_noalloc(int64_t n, const int32_t *src, const int32_t *dst, int6
  * cc_batch_run    one schedule for every graph (order, mode, check_interval as
  *                 for cc_run), or order == CC_ORDER_AUTO for a per-graph
  *                 schedule chosen by the learned scheduler (the plain order-2
- *                 synchronous schedule without loaded weights).  labels_out:
+ *                 synchronous schedule without loaded weights; with AUTO and
+ *                 check_interval 0 every graph is checked after every sweep,
+ *                 since a batch shares its convergence checks).  labels_out:
  *                 DEVICE int32[vtx_off[n_graphs]]; sweeps_out: HOST int32
  *                 [n_graphs] or NULL; solve_ms: NULL or the device time.
  *                 CC_ENOTCONVERGED if a graph reached max_sweeps.
@@ -315,6 +317,11 @@ cc_status cc_graph_set_stream(cc_graph *g, void *cuda_stream);
 
 /* Number of vertices and stored edges of a handle (either may be NULL). */
 cc_status cc_graph_info(const cc_graph *g, int64_t *n, int64_t *m);
+
+/* Device pointers of the handle's edge arrays (the borrowed input, or the
+ * handle's own copy after cc_init copied or cc_graph_reorder reordered it);
+ * valid until cc_free or the next cc_graph_reorder. */
+cc_status cc_graph_edges(const cc_graph *g, const void **src, const void **dst);
 
 /* Release a handle and every device buffer it owns.  NULL is ignored. */
 void cc_free(cc_graph *g);

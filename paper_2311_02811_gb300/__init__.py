@@ -22,7 +22,7 @@ __all__ = [
     "cc_batch_run", "cc_batch_set_schedule", "cc_batch_run_scheduled", "cc_batch_tuning",
     "cc_batch_set_tuning", "cc_batch_free", "cc_batch", "cc_sched_load", "cc_sched_blob_bytes",
     "cc_sched_param_count", "cc_sched_decode", "cc_graph_features", "cc_batch_features",
-    "cc_sched_predict", "cc_sched_train", "load_default_scheduler", "SCHED_WEIGHTS_PATH", "cc_sched_train_step", "CC_SCHED_FEATURES", "CC_SCHED_CLASSES", "cc_graph_info", "cc_graph_set_stream", "cc_graph_reorder", "CC_REORDER_SRC", "CC_REORDER_LOWDEG", "cc_strerror",
+    "cc_sched_predict", "cc_sched_train", "load_default_scheduler", "SCHED_WEIGHTS_PATH", "cc_sched_train_step", "CC_SCHED_FEATURES", "CC_SCHED_CLASSES", "cc_graph_info", "cc_graph_edges", "cc_graph_set_stream", "cc_graph_reorder", "CC_REORDER_SRC", "CC_REORDER_LOWDEG", "cc_strerror",
     "cc_last_error",
 ]
 
@@ -175,7 +175,7 @@ def cc_run(g, labels_out, order=2, mode=CC_ASYNC, check_interval=1, max_sweeps=1
 
 
 def cc_run_noalloc(n, src, dst, labels_out, order=2, mode=CC_ASYNC, check_interval=1,
-                   max_sweeps=1 << 20, stream=None, raise_on_error=True):
+                   max_sweeps=1 << 20, stream=None, raise_on_error=True, m=None):
     """cc_run without any device allocation (int32 device arrays); returns sweeps.
 
     See cc_run_noalloc in contour.h: for callers that must not allocate device
@@ -184,7 +184,8 @@ def cc_run_noalloc(n, src, dst, labels_out, order=2, mode=CC_ASYNC, check_interv
     pd, _ = _ptr(dst)
     po, _ = _ptr(labels_out)
     sw = _i32(0)
-    rc = lib.cc_run_noalloc(int(n), ps, pd, len(src) if src is not None else 0, int(order),
+    m = m if m is not None else (len(src) if src is not None else 0)
+    rc = lib.cc_run_noalloc(int(n), ps, pd, int(m), int(order),
                             int(mode), int(check_interval), int(max_sweeps), po,
                             ctypes.byref(sw), _stream(stream))
     if raise_on_error:
@@ -425,6 +426,17 @@ def cc_graph_reorder(g, method=CC_REORDER_LOWDEG):
     _check(lib.cc_graph_reorder(g, int(method)), "cc_graph_reorder")
     if isinstance(g, cc_graph):
         g._keep = ()  # the handle now owns its edges
+
+
+lib.cc_graph_edges.argtypes = [_p, ctypes.POINTER(_p), ctypes.POINTER(_p)]
+lib.cc_graph_edges.restype = _int
+
+
+def cc_graph_edges(g):
+    """(src, dst) device pointers (ints) of the handle's edge arrays."""
+    a, b = _p(), _p()
+    _check(lib.cc_graph_edges(g, ctypes.byref(a), ctypes.byref(b)), "cc_graph_edges")
+    return a.value, b.value
 
 
 def cc_graph_info(g):

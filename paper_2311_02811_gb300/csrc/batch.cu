@@ -303,9 +303,7 @@ __global__ void __launch_bounds__(kLargeThreads) batch_round_kernel(Dev d, int c
             viol = sync ? cc::mm_fixed<H, true, kEPT>(w, v, L, Lu) : cc::mm_fixed<H, false, kEPT>(w, v, L, Lu);
         } else {
             const int h = d.h[g];
-#pragma unroll 1
-            for (int k = 0; k < kEPT; ++k)
-                viol |= sync ? cc::mm_runtime<true>(w[k], v[k], h, L, Lu) : cc::mm_runtime<false>(w[k], v[k], h, L, Lu);
+            viol = sync ? cc::mm_runtime_ilp<true, kEPT>(w, v, h, L, Lu) : cc::mm_runtime_ilp<false, kEPT>(w, v, h, L, Lu);
         }
         const int any = __syncthreads_or(viol);
         if (threadIdx.x == 0 && any && checked) d.flag[g] = 1;

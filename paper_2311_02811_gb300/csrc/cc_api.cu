@@ -553,6 +553,13 @@ static cc_status run_impl(cc_graph* g, int order, int mode, int c, int32_t max_s
     return CC_OK;
 }
 
+extern "C" cc_status cc_graph_edges(const cc_graph* g, const void** src, const void** dst) {
+    if (!g) return set_error(CC_EINVAL, "cc_graph_edges: g is NULL");
+    if (src) *src = g->src;
+    if (dst) *dst = g->dst;
+    return CC_OK;
+}
+
 extern "C" cc_status cc_graph_info(const cc_graph* g, int64_t* n, int64_t* m) {
     if (!g) return set_error(CC_EINVAL, "cc_graph_info: g is NULL");
     if (n) *n = g->n;

@@ -166,6 +166,70 @@ __device__ __forceinline__ bool mm_runtime(IdT w, IdT v, int h, IdT* L, IdT* Lu)
     return viol;
 }
 
+// The same run-time order for K edges at once: the 2K chains advance in
+// lockstep, so each step issues up to 2K independent gathers; a chain stops
+// at its root.  The write-back walks the chains again in lockstep.
+template <bool SYNC, int K, typename IdT>
+__device__ __forceinline__ bool mm_runtime_ilp(const IdT (&w)[K], const IdT (&v)[K], int h, IdT* L, IdT* Lu) {
+    IdT cur[2 * K], first[2 * K];
+    unsigned act = 0;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        cur[2 * k] = w[k];
+        cur[2 * k + 1] = v[k];
+    }
+#pragma unroll
+    for (int i = 0; i < 2 * K; ++i) {
+        first[i] = rd<SYNC>(L, cur[i]);
+        if (first[i] != cur[i]) act |= 1u << i;
+        cur[i] = first[i];
+    }
+    for (int j = 1; j < h && act; ++j) {
+        IdT y[2 * K];
+#pragma unroll
+        for (int i = 0; i < 2 * K; ++i) y[i] = (act >> i & 1u) ? rd<SYNC>(L, cur[i]) : cur[i];
+#pragma unroll
+        for (int i = 0; i < 2 * K; ++i) {
+            if (y[i] == cur[i]) act &= ~(1u << i);
+            cur[i] = y[i];
+        }
+    }
+    bool viol = false;
+    IdT z[K];
+    unsigned wact = 0;  // chains that must be written
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        z[k] = cur[2 * k] < cur[2 * k + 1] ? cur[2 * k] : cur[2 * k + 1];
+        if (first[2 * k] > z[k]) wact |= 1u << (2 * k);
+        if (first[2 * k + 1] > z[k]) wact |= 1u << (2 * k + 1);
+    }
+    viol = wact != 0;
+    IdT x[2 * K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        x[2 * k] = w[k];
+        x[2 * k + 1] = v[k];
+    }
+    for (int j = 0; j < h && wact; ++j) {
+        IdT y[2 * K];
+#pragma unroll
+        for (int i = 0; i < 2 * K; ++i) y[i] = (wact >> i & 1u) ? rd<SYNC>(L, x[i]) : x[i];
+#pragma unroll
+        for (int i = 0; i < 2 * K; ++i) {
+            if (!(wact >> i & 1u)) continue;
+            const IdT zi = z[i >> 1];
+            if (y[i] <= zi) {  // labels further down the chain are <= y
+                wact &= ~(1u << i);
+                continue;
+            }
+            wr<SYNC>(L, Lu, x[i], zi);
+            if (y[i] == x[i]) wact &= ~(1u << i);  // root
+            x[i] = y[i];
+        }
+    }
+    return viol;
+}
+
 // ---------------------------------------------------------------------------
 // the sweep: every edge once (Alg. 1 edge loop)
 // ---------------------------------------------------------------------------
@@ -237,8 +301,7 @@ mm_sweep_kernel(const IdT* __restrict__ src, const IdT* __restrict__ dst, int64_
         if constexpr (H > 0) {
             viol |= mm_fixed<H, SYNC, 4 * G>(w, v, L, Lu);
         } else {
-#pragma unroll 1
-            for (int k = 0; k < 4 * G; ++k) viol |= mm_runtime<SYNC>(w[k], v[k], h, L, Lu);
+            viol |= mm_runtime_ilp<SYNC, 4 * G>(w, v, h, L, Lu);
         }
     }
     const int64_t tail0 = ngroups * 4 * G;

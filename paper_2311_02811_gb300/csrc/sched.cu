@@ -560,7 +560,12 @@ cc_status batch_resolve_schedule(cc_batch_plan* b, int mode, int c) {
             decode(x->h_cls[g], &o, &md, &ci);
             h[g] = o == CC_ORDER_FULL ? CC_MAX_ORDER : o;
             sync[g] = md == CC_SYNC;
-            cv[g] = c >= 1 ? c : ci;
+            // in a batch the convergence check is shared by all graphs of a
+            // round (and free in the shared-memory path), so the interval the
+            // model learned from single-graph runs -- where it saves check
+            // launches -- would only add sweeps: check every sweep
+            (void)ci;
+            cv[g] = c >= 1 ? c : 1;
         }
     }
     batch_set_schedule(b, h.data(), sync.data(), cv.data());
