@@ -39,7 +39,7 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--workload", default="rmat24",
-                   help="rmat<scale> (default rmat24), grid4096 or components64")
+                   help="rmat<scale> (default rmat24), grid4096, components64, batch<G> or delaunay-scaling")
     p.add_argument("--order", type=int, default=2)
     p.add_argument("--mode", choices=["async", "sync"], default="async")
     p.add_argument("--interval", type=int, default=1)
@@ -526,12 +526,51 @@ def run_batch(args, rank, world, local):
         print(json.dumps(line), flush=True)
 
 
+PAPER_DELAUNAY_GROWTH = {"C-2": 895, "C-1m1m": 1072, "C-m": 1268, "C-11mm": 1329, "C-Syn": 2705}
+
+
+def run_delaunay_scaling(args, rank):
+    """Solve time of each Contour variant on Delaunay-style graphs n = 2^10..2^24
+    and its growth from n10 to n24 (the paper's delaunay_n10..n24 experiment)."""
+    import paper_2311_02811_gb300 as cc
+    dev = torch.device("cuda", torch.cuda.current_device())
+    variants = {"C-Syn": (2, cc.CC_SYNC), "C-1": (1, cc.CC_ASYNC), "C-2": (2, cc.CC_ASYNC),
+                "C-m": (0, cc.CC_ASYNC), "C-11mm": (cc.CC_ORDER_11MM, cc.CC_ASYNC),
+                "C-1m1m": (cc.CC_ORDER_1M1M, cc.CC_ASYNC)}
+    rows = []
+    for k in range(10, 25):
+        n, s, d = gg.delaunay_like(k, device=dev)
+        g = cc.cc_init(n, s, d)
+        out = torch.empty(n, dtype=torch.int32, device=dev)
+        row = {"k": k, "n": n, "m": int(s.numel())}
+        for name, (order, mode) in variants.items():
+            best, sweeps = float("inf"), 0
+            for _ in range(1 + max(1, min(args.steps, 3))):
+                st = cc.cc_run(g, out, order, mode, 1)
+                if st.solve_ms < best:
+                    best, sweeps = st.solve_ms, st.sweeps
+            row[name] = {"ms": best, "sweeps": sweeps}
+        cc.cc_free(g)
+        rows.append(row)
+        del s, d, out
+    growth = {v: rows[-1][v]["ms"] / rows[0][v]["ms"] for v in variants}
+    line = {"metric": "Delaunay-style scaling n=2^10..2^24: solve-time growth n10 -> n24",
+            "value": growth["C-2"], "unit": "x", "higher_is_better": False, "n_gpus": 1,
+            "data": "synthetic", "dtype": "int32",
+            "config": {"workload": "delaunay-like-2^10..2^24", "edges": "jittered grid with Delaunay diagonals"},
+            "growth": growth, "paper_growth_20_core_xeon": PAPER_DELAUNAY_GROWTH, "rows": rows}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     rank, world, local = dist_init()
     try:
         if args.impl == "reference":
             run_reference(args, rank, world)
+        elif args.workload == "delaunay-scaling":
+            run_delaunay_scaling(args, rank)
         elif args.workload.startswith("batch"):
             run_batch(args, rank, world, local)
         else:

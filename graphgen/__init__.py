@@ -22,6 +22,8 @@ here, so these seeded families stand in for them):
 * ``caterpillar``  -- a path backbone with leaves hung on every backbone vertex;
 * ``components64`` -- 32 paths + 32 Erdos-Renyi graphs with a spanning path,
                       each on 1,024 vertices (65,536 vertices, 294,880 edges);
+* ``delaunay_like``-- planar triangulation of a jittered grid with Delaunay
+                      diagonals (n = 2^k, m ~ 3n, degree ~6);
 * ``batch_mix``    -- many independent graphs of log-uniform size drawn from
                       the four families above.
 
@@ -38,7 +40,7 @@ import torch
 
 __all__ = [
     "BASE_SEED", "mix64_int", "stream_key", "uniform64", "uniform_below",
-    "path", "grid", "rmat", "er", "caterpillar", "components64",
+    "path", "grid", "rmat", "er", "caterpillar", "components64", "delaunay_like",
     "batch_mix_params", "batch_graph", "batch_mix", "permute_and_shuffle",
 ]
 
@@ -303,6 +305,50 @@ def components64(seed: int = BASE_SEED, device="cpu", permute=True, id_dtype=tor
             parts_d.append(base + y)
     n = comp * (n_path + n_er)
     return n, *_finish(n, torch.cat(parts_s), torch.cat(parts_d), seed, permute, id_dtype)
+
+
+def delaunay_like(k: int, seed: int = BASE_SEED, device="cpu", permute=True, id_dtype=torch.int32,
+                  cell: int = 1024, jitter: int = 200):
+    """Delaunay-style planar triangulation with n = 2**k vertices, m ~ 3n.
+
+    Stand-in for the delaunay_n* family (Delaunay triangulations of random
+    points, near-uniform degree ~6).  Vertex (r, c) of an R x C grid
+    (R = 2**(k//2), C = 2**(k - k//2)) sits at integer point
+    (c*cell + jx, r*cell + jy) with jx, jy uniform in [-jitter, jitter].  Grid
+    edges are kept and every cell is split by the diagonal that satisfies the
+    empty-circumcircle (Delaunay) test for its four corners, evaluated exactly
+    in 64-bit integers, so the graph is identical on CPU and GPU.
+    """
+    R, C = 1 << (k // 2), 1 << (k - k // 2)
+    n = R * C
+    z = uniform64(stream_key(seed, 8), 0, n, device)
+    span = 2 * jitter + 1
+    jx = uniform_below(_hi32(z), span) - jitter
+    jy = uniform_below(_lo32(z), span) - jitter
+    idx = torch.arange(n, dtype=torch.int64, device=device)
+    r, c = idx // C, idx % C
+    px, py = c * cell + jx, r * cell + jy
+    # cells (r, c) for r < R-1, c < C-1; corners a=(r,c) b=(r,c+1) cc=(r+1,c+1) d=(r+1,c)
+    cr = torch.arange(R - 1, dtype=torch.int64, device=device).repeat_interleave(C - 1)
+    ccol = torch.arange(C - 1, dtype=torch.int64, device=device).repeat(R - 1)
+    a = cr * C + ccol
+    b = a + 1
+    cc_ = a + C + 1
+    d = a + C
+    # d inside the circumcircle of the counter-clockwise triangle (a, b, cc)?
+    ax, ay = px[a] - px[d], py[a] - py[d]
+    bx, by = px[b] - px[d], py[b] - py[d]
+    cx, cy = px[cc_] - px[d], py[cc_] - py[d]
+    a2, b2, c2 = ax * ax + ay * ay, bx * bx + by * by, cx * cx + cy * cy
+    det = ax * (by * c2 - b2 * cy) - ay * (bx * c2 - b2 * cx) + a2 * (bx * cy - by * cx)
+    flip = det > 0  # then the Delaunay diagonal is b-d, else a-cc
+    ds = torch.where(flip, b, a)
+    dd = torch.where(flip, d, cc_)
+    hs = (idx[c < C - 1])
+    vs = idx[r < R - 1]
+    s = torch.cat([hs, vs, ds])
+    t = torch.cat([hs + 1, vs + C, dd])
+    return n, *_finish(n, s, t, seed, permute, id_dtype)
 
 
 # ---------------------------------------------------------------------------

@@ -74,15 +74,26 @@ std::vector<unsigned char> g_blob;
 // features
 // ---------------------------------------------------------------------------
 
+// Per-CTA scratch of the feature kernel: an open-addressing table from the
+// sample's vertices to slots (at most 2 * kSample distinct vertices, so a
+// table of 4 * kSample slots stays at most half full), per-slot degree and
+// BFS words, the sample's edges as slot pairs, and the list of used slots.
+// The kernel returns every slot it used to empty, so the scratch is cleared
+// once when allocated and never again.
+constexpr int kSlots = 4 * kSample;
+
 struct FeatArgs {
     int32_t G;
     const int64_t* off_v;
     const int64_t* off_e;
     const int32_t* src;
     const int32_t* dst;
-    int32_t* deg;        // per-vertex scratch, all zero between uses
-    uint32_t* word;      // per-vertex BFS state, all zero between uses
-    int32_t* owned;      // per-CTA list of touched vertices (2 * kSample per CTA)
+    int32_t* keys;       // kSlots per CTA, -1 = empty
+    int32_t* deg;        // kSlots per CTA
+    uint32_t* word;      // kSlots per CTA: bits 0-7 visited, 8-15 frontier, 16-23 next
+    int32_t* su;         // kSample per CTA: slot of the sample edge's src
+    int32_t* sv;         // kSample per CTA: slot of its dst
+    int32_t* owned;      // 2 * kSample per CTA: slots in use
     float* out;          // G x kFeat
 };
 
@@ -90,20 +101,37 @@ __device__ __forceinline__ long long sample_pos(long long j, long long m, long l
     return (m <= S) ? j : (j * m) / S;
 }
 
+// Slot of vertex x; a new slot is appended to the used list.
+__device__ __forceinline__ int32_t table_slot(int32_t* keys, int32_t x, int32_t* owned, int32_t* n_owned) {
+    uint32_t h = ((uint32_t)x * 2654435761u) & (kSlots - 1);
+    for (int probe = 0; probe < kSlots; ++probe) {
+        const int32_t k = atomicCAS(keys + h, -1, x);
+        if (k == -1) {
+            owned[atomicAdd(n_owned, 1)] = (int32_t)h;
+            return (int32_t)h;
+        }
+        if (k == x) return (int32_t)h;
+        h = (h + 1) & (kSlots - 1);
+    }
+    return -1;  // unreachable: the table is at most half full
+}
+
 __global__ void __launch_bounds__(kFeatThreads) features_kernel(FeatArgs a) {
     __shared__ int32_t s_owned;
     __shared__ unsigned long long s_sumsq;
     __shared__ int32_t s_max;
     __shared__ int32_t s_ecc[8];
+    int32_t* keys = a.keys + (size_t)blockIdx.x * kSlots;
+    int32_t* deg = a.deg + (size_t)blockIdx.x * kSlots;
+    uint32_t* word = a.word + (size_t)blockIdx.x * kSlots;
+    int32_t* su = a.su + (size_t)blockIdx.x * kSample;
+    int32_t* sv = a.sv + (size_t)blockIdx.x * kSample;
     int32_t* owned = a.owned + (size_t)blockIdx.x * 2 * kSample;
     for (int32_t g = blockIdx.x; g < a.G; g += gridDim.x) {
-        const long long base_v = a.off_v[g];
-        const long long n = a.off_v[g + 1] - base_v;
+        const long long n = a.off_v[g + 1] - a.off_v[g];
         const long long e0 = a.off_e[g];
         const long long m = a.off_e[g + 1] - e0;
         const long long S = m < kSample ? m : kSample;
-        int32_t* deg = a.deg + base_v;
-        uint32_t* word = a.word + base_v;
         if (threadIdx.x == 0) {
             s_owned = 0;
             s_sumsq = 0;
@@ -111,12 +139,15 @@ __global__ void __launch_bounds__(kFeatThreads) features_kernel(FeatArgs a) {
         }
         if (threadIdx.x < 8) s_ecc[threadIdx.x] = 0;
         __syncthreads();
-        // degrees on the sample; the first thread to touch a vertex owns it
+        // sample edges -> slots; degrees on the sample
         for (long long j = threadIdx.x; j < S; j += blockDim.x) {
             const long long e = e0 + sample_pos(j, m, S);
-            const int32_t u = a.src[e], v = a.dst[e];
-            if (atomicAdd(deg + u, 1) == 0) owned[atomicAdd(&s_owned, 1)] = u;
-            if (atomicAdd(deg + v, 1) == 0) owned[atomicAdd(&s_owned, 1)] = v;
+            const int32_t pu = table_slot(keys, a.src[e], owned, &s_owned);
+            const int32_t pv = table_slot(keys, a.dst[e], owned, &s_owned);
+            su[j] = pu;
+            sv[j] = pv;
+            atomicAdd(deg + pu, 1);
+            atomicAdd(deg + pv, 1);
         }
         __syncthreads();
         const int32_t no = s_owned;
@@ -129,22 +160,20 @@ __global__ void __launch_bounds__(kFeatThreads) features_kernel(FeatArgs a) {
         }
         atomicAdd(&s_sumsq, sq);
         atomicMax(&s_max, mx);
-        // 8 BFS sources, one bit each (bits 0-7 visited, 8-15 frontier, 16-23 next)
+        // 8 BFS sources: the src endpoints of sample positions floor((2i+1) S / 16)
         if (threadIdx.x < 8 && S > 0) {
             const long long j = ((2ll * threadIdx.x + 1) * S) / 16;
-            const int32_t sv = a.src[e0 + sample_pos(j, m, S)];
-            atomicOr(word + sv, (1u << threadIdx.x) | (1u << (8 + threadIdx.x)));
+            atomicOr(word + su[j], (1u << threadIdx.x) | (1u << (8 + threadIdx.x)));
         }
         __syncthreads();
         for (int level = 1; level <= kLevels; ++level) {
             for (long long j = threadIdx.x; j < S; j += blockDim.x) {
-                const long long e = e0 + sample_pos(j, m, S);
-                const int32_t u = a.src[e], v = a.dst[e];
-                const uint32_t wu = word[u], wv = word[v];
+                const int32_t pu = su[j], pv = sv[j];
+                const uint32_t wu = word[pu], wv = word[pv];
                 const uint32_t to_v = ((wu >> 8) & 0xffu) & ~(wv & 0xffu);
                 const uint32_t to_u = ((wv >> 8) & 0xffu) & ~(wu & 0xffu);
-                if (to_v) atomicOr(word + v, to_v << 16);
-                if (to_u) atomicOr(word + u, to_u << 16);
+                if (to_v) atomicOr(word + pv, to_v << 16);
+                if (to_u) atomicOr(word + pu, to_u << 16);
             }
             __syncthreads();
             int any = 0;
@@ -161,10 +190,12 @@ __global__ void __launch_bounds__(kFeatThreads) features_kernel(FeatArgs a) {
             }
             if (__syncthreads_or(any) == 0) break;
         }
-        // leave the scratch zero for the next graph / call
+        // return every used slot to empty for the next graph / call
         for (int32_t i = threadIdx.x; i < no; i += blockDim.x) {
-            deg[owned[i]] = 0;
-            word[owned[i]] = 0;
+            const int32_t x = owned[i];
+            keys[x] = -1;
+            deg[x] = 0;
+            word[x] = 0;
         }
         if (threadIdx.x == 0) {
             float* f = a.out + (size_t)g * kFeat;
@@ -404,14 +435,9 @@ namespace cc {
 // scratch of the feature kernel (zeroed once; the kernel leaves it zero).
 struct SchedCtx {
     int32_t G = 0;
-    int64_t total_n = 0;
     int64_t* d_off = nullptr;  // off_v[G+1] then off_e[G+1]
     float* d_feat = nullptr;   // G x kFeat
     int32_t* d_cls = nullptr;  // G
-    int32_t* deg = nullptr;
-    uint32_t* word = nullptr;
-    int32_t* owned = nullptr;
-    int grid = 0;
     std::vector<int32_t> h_cls;  // host copy of the classes
     long long version = -1;    // model version h_cls was computed with
 };
@@ -421,9 +447,6 @@ void sched_ctx_free(SchedCtx* c) {
     cudaFree(c->d_off);
     cudaFree(c->d_feat);
     cudaFree(c->d_cls);
-    cudaFree(c->deg);
-    cudaFree(c->word);
-    cudaFree(c->owned);
     delete c;
 }
 
@@ -431,23 +454,50 @@ void sched_ctx_free(SchedCtx* c) {
 
 namespace {
 
+// Process-wide feature scratch for up to g_scratch_ctas CTAs (guarded by g_mu).
+struct Scratch {
+    int ctas = 0;
+    int32_t* keys = nullptr;
+    int32_t* deg = nullptr;
+    uint32_t* word = nullptr;
+    int32_t* su = nullptr;
+    int32_t* sv = nullptr;
+    int32_t* owned = nullptr;
+} g_scratch;
+
+cc_status scratch_get(int ctas, cudaStream_t s) {
+    if (g_scratch.ctas >= ctas) return CC_OK;
+    cudaFree(g_scratch.keys);
+    cudaFree(g_scratch.deg);
+    cudaFree(g_scratch.word);
+    cudaFree(g_scratch.su);
+    cudaFree(g_scratch.sv);
+    cudaFree(g_scratch.owned);
+    g_scratch = Scratch();
+    const size_t T = (size_t)ctas * kSlots, S = (size_t)ctas * kSample;
+    cudaError_t e = cudaMalloc(&g_scratch.keys, T * sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaMalloc(&g_scratch.deg, T * sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaMalloc(&g_scratch.word, T * sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMalloc(&g_scratch.su, S * sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaMalloc(&g_scratch.sv, S * sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaMalloc(&g_scratch.owned, 2 * S * sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaMemsetAsync(g_scratch.keys, 0xff, T * sizeof(int32_t), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(g_scratch.deg, 0, T * sizeof(int32_t), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(g_scratch.word, 0, T * sizeof(uint32_t), s);
+    if (e != cudaSuccess) return cc::cuda_fail(e, "scheduler scratch", __FILE__, __LINE__);
+    g_scratch.ctas = ctas;
+    return CC_OK;
+}
+
 cc_status ctx_get(cc::SchedCtx** slot, int32_t G, const int64_t* off_v, const int64_t* off_e, cudaStream_t s) {
     if (*slot) return CC_OK;
     cc::SchedCtx* c = new (std::nothrow) cc::SchedCtx();
     if (!c) return cc::set_error(CC_ENOMEM, "scheduler context");
     c->G = G;
-    c->total_n = off_v[G];
-    c->grid = std::max(1, std::min<int>(G, cc::device_sms() * 2));
-    const size_t nv = (size_t)std::max<int64_t>(c->total_n, 1);
     cudaError_t e = cudaMalloc(&c->d_off, 2 * (size_t)(G + 1) * sizeof(int64_t));
     if (e == cudaSuccess) e = cudaMalloc(&c->d_feat, (size_t)std::max(G, 1) * kFeat * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc(&c->d_cls, (size_t)std::max(G, 1) * sizeof(int32_t));
-    if (e == cudaSuccess) e = cudaMalloc(&c->deg, nv * sizeof(int32_t));
-    if (e == cudaSuccess) e = cudaMalloc(&c->word, nv * sizeof(uint32_t));
-    if (e == cudaSuccess) e = cudaMalloc(&c->owned, (size_t)c->grid * 2 * kSample * sizeof(int32_t));
     c->h_cls.assign((size_t)std::max(G, 1), 0);
-    if (e == cudaSuccess) e = cudaMemsetAsync(c->deg, 0, nv * sizeof(int32_t), s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(c->word, 0, nv * sizeof(uint32_t), s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_off, off_v, (G + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(c->d_off + G + 1, off_e, (G + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s);
@@ -460,11 +510,15 @@ cc_status ctx_get(cc::SchedCtx** slot, int32_t G, const int64_t* off_v, const in
     return CC_OK;
 }
 
-// Features of every graph of the context into c->d_feat.
+// Features of every graph of the context into c->d_feat (caller holds g_mu).
 cc_status run_features(cc::SchedCtx* c, const int32_t* src, const int32_t* dst, cudaStream_t s) {
     if (c->G == 0) return CC_OK;
-    FeatArgs a{c->G, c->d_off, c->d_off + c->G + 1, src, dst, c->deg, c->word, c->owned, c->d_feat};
-    features_kernel<<<c->grid, kFeatThreads, 0, s>>>(a);
+    const int grid = std::max(1, std::min<int>(c->G, cc::device_sms() * 2));
+    cc_status st = scratch_get(grid, s);
+    if (st != CC_OK) return st;
+    FeatArgs a{c->G, c->d_off, c->d_off + c->G + 1, src, dst, g_scratch.keys, g_scratch.deg, g_scratch.word,
+               g_scratch.su, g_scratch.sv, g_scratch.owned, c->d_feat};
+    features_kernel<<<grid, kFeatThreads, 0, s>>>(a);
     SCUDA(cudaGetLastError());
     return CC_OK;
 }
@@ -602,6 +656,8 @@ extern "C" cc_status cc_sched_decode(int32_t cls, int* order, int* mode, int* ch
 extern "C" cc_status cc_graph_features(cc_graph* g, float* features_out) {
     if (!g || !features_out) return cc::set_error(CC_EINVAL, "cc_graph_features: NULL argument");
     if (cc::graph_id_bits(g) != 32) return cc::set_error(CC_EINVAL, "cc_graph_features: int32 ids only");
+    // the feature scratch is shared: each use completes before the lock is released
+    std::lock_guard<std::mutex> lock(g_mu);
     long long n = 0, m = 0;
     cc::graph_nm(g, &n, &m);
     cudaStream_t s = cc::graph_stream(g);
@@ -621,6 +677,7 @@ extern "C" cc_status cc_batch_features(cc_batch_plan* b, float* features_out) {
     if (!b || !features_out) return cc::set_error(CC_EINVAL, "cc_batch_features: NULL argument");
     const int32_t G = cc::batch_graph_count(b);
     if (G == 0) return CC_OK;
+    std::lock_guard<std::mutex> lock(g_mu);
     cudaStream_t s = cc::batch_stream(b);
     cc::SchedCtx** slot = cc::batch_sched_slot(b);
     cc_status st = ctx_get(slot, G, cc::batch_off_v(b), cc::batch_off_e(b), s);

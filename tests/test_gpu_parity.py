@@ -319,3 +319,18 @@ def test_per_iteration_order_schedules(cc, sched):
         for c in (1, 4):  # the interval is ignored: schedules check every sweep
             got, st, _ = solve(cc, n, s, d, code, cc.CC_ASYNC, c)
             assert (got == want).all() and st.check_interval == 1
+
+
+def test_generators_bit_identical_on_gpu():
+    """The seeded generators produce the same graphs on the GPU as on the CPU."""
+    makers = [lambda dev: gg.rmat(14, device=dev), lambda dev: gg.grid(90, 110, device=dev),
+              lambda dev: gg.delaunay_like(13, device=dev)[1:], lambda dev: gg.er(9000, 30000, device=dev),
+              lambda dev: gg.caterpillar(500, device=dev), lambda dev: gg.components64(device=dev)[1:]]
+    for make in makers:
+        a, b = make("cpu")
+        c, d = make("cuda")
+        assert torch.equal(a, c.cpu()) and torch.equal(b, d.cpu())
+    v1, e1, s1, d1, _ = gg.batch_mix(16, device="cpu", n_hi=2e4)
+    v2, e2, s2, d2, _ = gg.batch_mix(16, device="cuda", n_hi=2e4)
+    assert torch.equal(v1, v2) and torch.equal(e1, e2)
+    assert torch.equal(s1, s2.cpu()) and torch.equal(d1, d2.cpu())
