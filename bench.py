@@ -446,6 +446,11 @@ def batch_compare(cc, G, args, dev, stream, seed):
     t0 = time.perf_counter()
     plan = cc.cc_batch_init(vo, eo, s, d, autotune=1, stream=stream.cuda_stream)
     tune_s = time.perf_counter() - t0
+    reorder_s = None
+    if args.reorder != "none":
+        t0 = time.perf_counter()
+        cc.cc_batch_reorder(plan)
+        reorder_s = time.perf_counter() - t0
     out_b = torch.empty(total_n, dtype=torch.int32, device=dev)
     res = {}
 
@@ -478,9 +483,11 @@ def batch_compare(cc, G, args, dev, stream, seed):
         identical_learned = bool(torch.equal(out_b, ref))
         cc.cc_sched_load(None)
     handles = []
+    ps, pd = cc.cc_batch_edges(plan)  # the same (possibly reordered) edges as the batched form
     for g in range(G):
         a, b = int(eo[g]), int(eo[g + 1])
-        handles.append((cc.cc_init(int(vo[g + 1] - vo[g]), s[a:b], d[a:b], stream=stream.cuda_stream),
+        handles.append((cc.cc_init(int(vo[g + 1] - vo[g]), ps + 4 * a, pd + 4 * a, m=b - a, id_bits=32,
+                                   on_device=True, stream=stream.cuda_stream),
                         int(vo[g]), int(vo[g + 1])))
     out_p = torch.empty(total_n, dtype=torch.int32, device=dev)
 
@@ -500,6 +507,9 @@ def batch_compare(cc, G, args, dev, stream, seed):
     best_batched = "batched-learned" if learned else "batched-c2-async"
     return {"workload": f"batch-mix-{G}", "graphs": G, "n": total_n, "m": total_m,
             "generation_s": gen_s, "plan_and_autotune_s": tune_s,
+            "edge_order": ("as generated (shuffled)" if reorder_s is None else
+                           f"cc_batch_reorder once before timing ({reorder_s:.2f} s); the plain "
+                           "per-graph handles use the same reordered edges"),
             "tuning": {"smem_budget": tuning[0], "threads": tuning[1], "edges_per_thread": tuning[2]},
             "forms": res, "identical_output": identical,
             "speedup_batched_learned_vs_plain": res["plain-o2-sync"]["ms"] / res[best_batched]["ms"],

@@ -237,6 +237,15 @@ cc_status cc_batch_tuning(const cc_batch_plan *b, int32_t *smem_budget, int32_t 
  * per thread 1..4. */
 cc_status cc_batch_set_tuning(cc_batch_plan *b, int32_t smem_budget, int32_t threads,
                               int32_t edges_per_thread);
+/* One-time layout step for a plan (see cc_graph_reorder): within every graph,
+ * edges are oriented from their lower-degree endpoint and grouped by it.  Each
+ * graph keeps its own edge range and its labels are unchanged.  The plan then
+ * owns the reordered copy (the borrowed arrays are no longer referenced).
+ * Batches of at most 2^32 - 1 vertices.  Synchronises the plan's stream. */
+cc_status cc_batch_reorder(cc_batch_plan *b);
+/* Device pointers of the plan's edge arrays (borrowed, or its own reordered
+ * copy); valid until cc_batch_free or the next cc_batch_reorder. */
+cc_status cc_batch_edges(const cc_batch_plan *b, const int32_t **src, const int32_t **dst);
 void cc_batch_free(cc_batch_plan *b);
 cc_status cc_batch(int32_t n_graphs, const int64_t *vtx_off, const int64_t *edge_off,
                    const int32_t *src, const int32_t *dst, int order, int mode, int check_interval,

@@ -20,7 +20,7 @@ __all__ = [
     "CC_ORDER_FULL", "CC_ORDER_AUTO", "CC_ORDER_11MM", "CC_ORDER_1M1M", "CC_NOALLOC_MAX_N", "CCError", "cc_stats", "cc_graph", "lib", "LIB_PATH",
     "cc_init", "cc_run", "cc_run_noalloc", "cc_free", "cc_batch_plan", "cc_batch_init",
     "cc_batch_run", "cc_batch_set_schedule", "cc_batch_run_scheduled", "cc_batch_tuning",
-    "cc_batch_set_tuning", "cc_batch_free", "cc_batch", "cc_sched_load", "cc_sched_blob_bytes",
+    "cc_batch_set_tuning", "cc_batch_reorder", "cc_batch_edges", "cc_batch_free", "cc_batch", "cc_sched_load", "cc_sched_blob_bytes",
     "cc_sched_param_count", "cc_sched_decode", "cc_graph_features", "cc_batch_features",
     "cc_sched_predict", "cc_sched_train", "load_default_scheduler", "SCHED_WEIGHTS_PATH", "cc_sched_train_step", "CC_SCHED_FEATURES", "CC_SCHED_CLASSES", "cc_graph_info", "cc_graph_edges", "cc_graph_set_stream", "cc_graph_reorder", "CC_REORDER_SRC", "CC_REORDER_LOWDEG", "cc_strerror",
     "cc_last_error",
@@ -290,6 +290,28 @@ def cc_batch_tuning(b):
 def cc_batch_set_tuning(b, smem_budget, threads=512, edges_per_thread=4):
     _check(lib.cc_batch_set_tuning(b, int(smem_budget), int(threads), int(edges_per_thread)),
            "cc_batch_set_tuning")
+
+
+lib.cc_batch_reorder.argtypes = [_p]
+lib.cc_batch_reorder.restype = _int
+
+
+def cc_batch_reorder(b):
+    """Group every graph's edges by its lower-degree endpoint (labels unchanged)."""
+    _check(lib.cc_batch_reorder(b), "cc_batch_reorder")
+    if isinstance(b, cc_batch_plan):
+        b._keep = ()
+
+
+lib.cc_batch_edges.argtypes = [_p, ctypes.POINTER(_p), ctypes.POINTER(_p)]
+lib.cc_batch_edges.restype = _int
+
+
+def cc_batch_edges(b):
+    """(src, dst) device pointers (ints) of the plan's edge arrays."""
+    a, c = _p(), _p()
+    _check(lib.cc_batch_edges(b, ctypes.byref(a), ctypes.byref(c)), "cc_batch_edges")
+    return a.value, c.value
 
 
 def cc_batch_free(b):

@@ -18,6 +18,7 @@
 //    (Section III-B2), retires converged graphs and rebuilds the active
 //    lists and tile prefix sums for the next round.
 // No kernel waits on another CTA; rounds are separated by kernel boundaries.
+#include <cub/device/device_radix_sort.cuh>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -556,6 +557,99 @@ __global__ void __launch_bounds__(256) batch_validate_kernel(const int64_t* off_
     if ((threadIdx.x & 31) == 0 && bad) atomicAdd(&ctl->bad_count, bad);
 }
 
+// Edge tiles over all graphs (epre = tile prefix per graph): the graph of a
+// tile and the local edge range it covers.
+__device__ __forceinline__ void tile_range(const int64_t* off_e, const long long* epre, int32_t G, long long t,
+                                           int32_t* g_out, long long* e0, long long* e1) {
+    int lo = 0, hi = G;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (epre[mid] <= t) lo = mid; else hi = mid;
+    }
+    *g_out = lo;
+    *e0 = off_e[lo] + (t - epre[lo]) * kTile;
+    *e1 = min((long long)off_e[lo + 1], *e0 + kTile);
+}
+
+// degrees of every vertex of the batch, indexed by global vertex id
+__global__ void __launch_bounds__(256) batch_degree_kernel(const int64_t* off_v, const int64_t* off_e,
+                                                          const int32_t* src, const int32_t* dst,
+                                                          const long long* epre, int32_t G, long long total,
+                                                          int32_t* deg) {
+    __shared__ int32_t s_g;
+    __shared__ long long s_e0, s_e1;
+    for (long long t = blockIdx.x; t < total; t += gridDim.x) {
+        if (threadIdx.x == 0) {
+            int32_t g;
+            long long e0, e1;
+            tile_range(off_e, epre, G, t, &g, &e0, &e1);
+            s_g = g;
+            s_e0 = e0;
+            s_e1 = e1;
+        }
+        __syncthreads();
+        const long long base = off_v[s_g];
+        for (long long e = s_e0 + threadIdx.x; e < s_e1; e += blockDim.x) {
+            atomicAdd(deg + base + src[e], 1);
+            atomicAdd(deg + base + dst[e], 1);
+        }
+        __syncthreads();
+    }
+}
+
+// key = global id of the lower-degree endpoint (ties: smaller id), value = the
+// other endpoint's local id.  Sorting by key keeps every graph's edges inside
+// its own edge range, because graphs own consecutive vertex ranges.
+__global__ void __launch_bounds__(256) batch_orient_kernel(const int64_t* off_v, const int64_t* off_e,
+                                                          const int32_t* src, const int32_t* dst,
+                                                          const long long* epre, int32_t G, long long total,
+                                                          const int32_t* deg, uint32_t* key, uint32_t* val) {
+    __shared__ int32_t s_g;
+    __shared__ long long s_e0, s_e1;
+    for (long long t = blockIdx.x; t < total; t += gridDim.x) {
+        if (threadIdx.x == 0) {
+            int32_t g;
+            long long e0, e1;
+            tile_range(off_e, epre, G, t, &g, &e0, &e1);
+            s_g = g;
+            s_e0 = e0;
+            s_e1 = e1;
+        }
+        __syncthreads();
+        const long long base = off_v[s_g];
+        for (long long e = s_e0 + threadIdx.x; e < s_e1; e += blockDim.x) {
+            const int32_t a = src[e], b = dst[e];
+            const int32_t da = deg[base + a], db = deg[base + b];
+            const bool swap = db < da || (db == da && b < a);
+            key[e] = (uint32_t)(base + (swap ? b : a));
+            val[e] = (uint32_t)(swap ? a : b);
+        }
+        __syncthreads();
+    }
+}
+
+// key (global id) -> local id of the graph that owns edge e
+__global__ void __launch_bounds__(256) batch_localize_kernel(const int64_t* off_v, const int64_t* off_e,
+                                                            const long long* epre, int32_t G, long long total,
+                                                            uint32_t* key) {
+    __shared__ int32_t s_g;
+    __shared__ long long s_e0, s_e1;
+    for (long long t = blockIdx.x; t < total; t += gridDim.x) {
+        if (threadIdx.x == 0) {
+            int32_t g;
+            long long e0, e1;
+            tile_range(off_e, epre, G, t, &g, &e0, &e1);
+            s_g = g;
+            s_e0 = e0;
+            s_e1 = e1;
+        }
+        __syncthreads();
+        const long long base = off_v[s_g];
+        for (long long e = s_e0 + threadIdx.x; e < s_e1; e += blockDim.x) key[e] = (uint32_t)((long long)key[e] - base);
+        __syncthreads();
+    }
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -575,6 +669,7 @@ struct cc_batch_plan {
     int64_t total_n = 0, total_m = 0;
     const int32_t* src = nullptr;
     const int32_t* dst = nullptr;
+    bool own_edges = false;  // after cc_batch_reorder
     cudaStream_t stream = nullptr;
     cudaStream_t cap = nullptr;
     // device buffers
@@ -613,6 +708,10 @@ void destroy_batch(cc_batch_plan* b) {
     for (auto& l : b->loops) {
         if (l.exec) cudaGraphExecDestroy(l.exec);
         if (l.graph) cudaGraphDestroy(l.graph);
+    }
+    if (b->own_edges) {
+        cudaFree(const_cast<int32_t*>(b->src));
+        cudaFree(const_cast<int32_t*>(b->dst));
     }
     cudaFree(b->d_off_v);
     cudaFree(b->d_off_e);
@@ -672,7 +771,9 @@ Dev make_dev(const cc_batch_plan* b, int32_t* L, std::vector<int32_t>& lists_h, 
     // host-side classification (lists are uploaded by the caller)
     const size_t S = G + 1;
     lists_h.assign(12 * S, 0);
-    pre_h.assign(7 * S, 0);
+    // slots 0-5 of the prefix buffer (slot 6 holds the edge-tile prefix of
+    // all graphs, written once by cc_batch_init and never overwritten)
+    pre_h.assign(6 * S, 0);
     std::vector<int32_t> small, large_all, cls[kClasses];
     for (int32_t g = 0; g < G; ++g) {
         if (is_small(b, g, b->small_budget, b->h_sync[g] != 0)) small.push_back(g);
@@ -805,6 +906,7 @@ namespace cc {
 // Runs one solve of the batch with the schedule in b->h_h/h_sync/h_c.
 cc_status batch_solve(cc_batch_plan* b, int32_t max_sweeps, int32_t* labels_out, int32_t* sweeps_out,
                       double* solve_ms) {
+    NvtxRange range("cc_batch_run");
     const int32_t G = b->G;
     cudaStream_t s = b->stream;
     const bool any_sync = std::any_of(b->h_sync.begin(), b->h_sync.end(), [](int32_t x) { return x != 0; });
@@ -1156,6 +1258,104 @@ extern "C" cc_status cc_batch_set_tuning(cc_batch_plan* b, int32_t smem_budget, 
     b->small_budget = smem_budget;
     b->small_threads = threads;
     b->small_ept = ept;
+    return CC_OK;
+}
+
+extern "C" cc_status cc_batch_reorder(cc_batch_plan* b) {
+    cc::NvtxRange range("cc_batch_reorder");
+    if (!b) return cc::set_error(CC_EINVAL, "cc_batch_reorder: batch is NULL");
+    if (b->total_m == 0) return CC_OK;
+    if (b->total_n >= (1ll << 32)) return cc::set_error(CC_EINVAL, "cc_batch_reorder: batches of >= 2^32 vertices are not supported");
+    const int32_t G = b->G;
+    const long long m = b->total_m;
+    cudaStream_t s = b->stream;
+    // edge-tile prefix of all graphs, rebuilt from the host offsets
+    long long* d_epre = b->d_pre + 6ull * (G + 1);
+    std::vector<long long> epre(G + 1, 0);
+    for (int32_t g = 0; g < G; ++g) epre[g + 1] = epre[g] + (b->off_e[g + 1] - b->off_e[g] + kTile - 1) / kTile;
+    const long long total_tiles = epre[G];
+    {
+        cudaError_t e0 = cudaMemcpyAsync(d_epre, epre.data(), (G + 1) * sizeof(long long), cudaMemcpyHostToDevice, s);
+        if (e0 != cudaSuccess) return cc::cuda_fail(e0, "cc_batch_reorder", __FILE__, __LINE__);
+    }
+    int bits = 1;
+    while (bits < 32 && (1ll << bits) < b->total_n) ++bits;
+    cc_status st = CC_OK;
+    uint32_t *k_in = nullptr, *v_in = nullptr, *k_out = nullptr, *v_out = nullptr;
+    int32_t* deg = nullptr;
+    void* tmp = nullptr;
+    size_t tmp_bytes = 0;
+    const int grid = cc::device_sms() * 8;
+    cudaError_t e = cudaMalloc(&k_in, (size_t)m * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&v_in, (size_t)m * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&k_out, (size_t)m * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&v_out, (size_t)m * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&deg, (size_t)b->total_n * 4);
+    if (e == cudaSuccess) e = cudaMemsetAsync(deg, 0, (size_t)b->total_n * 4, s);
+    if (e == cudaSuccess) {
+        batch_degree_kernel<<<grid, 256, 0, s>>>(b->d_off_v, b->d_off_e, b->src, b->dst, d_epre, G, total_tiles, deg);
+        batch_orient_kernel<<<grid, 256, 0, s>>>(b->d_off_v, b->d_off_e, b->src, b->dst, d_epre, G, total_tiles, deg,
+                                                 k_in, v_in);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cub::DeviceRadixSort::SortPairs(nullptr, tmp_bytes, k_in, k_out, v_in, v_out, m, 0, bits, s);
+    if (e == cudaSuccess) e = cudaMalloc(&tmp, tmp_bytes);
+    if (e == cudaSuccess) e = cub::DeviceRadixSort::SortPairs(tmp, tmp_bytes, k_in, k_out, v_in, v_out, m, 0, bits, s);
+    if (e == cudaSuccess) {
+        batch_localize_kernel<<<grid, 256, 0, s>>>(b->d_off_v, b->d_off_e, d_epre, G, total_tiles, k_out);
+        e = cudaGetLastError();
+    }
+    // every reordered id must still lie in its graph's [0, n) before any
+    // sweep gathers with it
+    if (e == cudaSuccess) {
+        BatchCtl zero = {};
+        zero.first_bad = ~0ull;
+        e = cudaMemcpyAsync(b->d_ctl, &zero, sizeof zero, cudaMemcpyHostToDevice, s);
+    }
+    if (e == cudaSuccess) {
+        const int gv = persistent_grid(reinterpret_cast<const void*>(batch_validate_kernel), 256, 0);
+        batch_validate_kernel<<<gv, 256, 0, s>>>(b->d_off_v, b->d_off_e, reinterpret_cast<const int32_t*>(k_out),
+                                                 reinterpret_cast<const int32_t*>(v_out), d_epre, G, total_tiles, b->d_ctl);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(b->h_ctl, b->d_ctl, sizeof(BatchCtl), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) st = cc::cuda_fail(e, "cc_batch_reorder", __FILE__, __LINE__);
+    if (st == CC_OK && b->h_ctl->bad_count)
+        st = cc::set_error(CC_ECUDA, "cc_batch_reorder: internal error, %llu reordered ids out of range",
+                           b->h_ctl->bad_count);
+    cudaFree(k_in);
+    cudaFree(v_in);
+    cudaFree(deg);
+    cudaFree(tmp);
+    if (st != CC_OK) {
+        cudaFree(k_out);
+        cudaFree(v_out);
+        return st;
+    }
+    // the plan now owns the reordered arrays; cached round graphs and
+    // scheduler features referred to the old ones
+    if (b->own_edges) {
+        cudaFree(const_cast<int32_t*>(b->src));
+        cudaFree(const_cast<int32_t*>(b->dst));
+    }
+    b->src = reinterpret_cast<const int32_t*>(k_out);
+    b->dst = reinterpret_cast<const int32_t*>(v_out);
+    b->own_edges = true;
+    for (auto& l : b->loops) {
+        if (l.exec) cudaGraphExecDestroy(l.exec);
+        if (l.graph) cudaGraphDestroy(l.graph);
+    }
+    b->loops.clear();
+    cc::sched_ctx_free(b->sched);
+    b->sched = nullptr;
+    return CC_OK;
+}
+
+extern "C" cc_status cc_batch_edges(const cc_batch_plan* b, const int32_t** src, const int32_t** dst) {
+    if (!b) return cc::set_error(CC_EINVAL, "cc_batch_edges: batch is NULL");
+    if (src) *src = b->src;
+    if (dst) *dst = b->dst;
     return CC_OK;
 }
 

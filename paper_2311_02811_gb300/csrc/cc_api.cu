@@ -379,6 +379,7 @@ static cc_status init_edges(cc_graph* g, int layout, const void* a, const void* 
 
 extern "C" cc_status cc_init(cc_graph** out, int64_t n, int id_bits, int layout, const void* a,
                              const void* b, int64_t cnt, int on_device, void* cuda_stream) {
+    cc::NvtxRange range("cc_init");
     g_last_error.clear();
     if (!out) return set_error(CC_EINVAL, "cc_init: g is NULL");
     *out = nullptr;
@@ -469,6 +470,7 @@ extern "C" cc_status cc_graph_set_stream(cc_graph* g, void* cuda_stream) {
 static cc_status run_impl(cc_graph* g, int order, int mode, int c, int32_t max_sweeps,
                           const void* init_labels, void* labels_out, int out_on_device,
                           cc_stats* stats, cudaStream_t s) {
+    cc::NvtxRange range("cc_run");
     g_last_error.clear();
     if (!g) return set_error(CC_EINVAL, "cc_run: g is NULL");
     if (g->n > 0 && !labels_out) return set_error(CC_EINVAL, "cc_run: labels_out is NULL");

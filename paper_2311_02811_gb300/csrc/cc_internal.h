@@ -2,12 +2,19 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <stdint.h>
 
 #include "../../include/contour.h"
 
 namespace cc {
+
+// NVTX range for profilers (a no-op unless a tool is attached).
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+};
 
 struct SchedCtx;  // scheduler buffers of a handle or plan (sched.cu)
 void sched_ctx_free(SchedCtx* c);

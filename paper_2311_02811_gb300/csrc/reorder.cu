@@ -42,6 +42,15 @@ __global__ void orient_kernel(const int32_t* src, const int32_t* dst, int64_t m,
     }
 }
 
+__global__ void range_check_kernel(const uint32_t* a, const uint32_t* b, int64_t m, int64_t n,
+                                   unsigned long long* bad) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    unsigned long long cnt = 0;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += stride)
+        cnt += ((int64_t)a[e] >= n) + ((int64_t)b[e] >= n);
+    if (cnt) atomicAdd(bad, cnt);
+}
+
 int bits_for(int64_t n) {
     int b = 1;
     while (b < 31 && (int64_t(1) << b) < n) ++b;
@@ -60,6 +69,7 @@ int bits_for(int64_t n) {
 }  // namespace
 
 extern "C" cc_status cc_graph_reorder(cc_graph* g, int method) {
+    cc::NvtxRange range("cc_graph_reorder");
     if (!g) return cc::set_error(CC_EINVAL, "cc_graph_reorder: g is NULL");
     if (method != CC_REORDER_SRC && method != CC_REORDER_LOWDEG)
         return cc::set_error(CC_EINVAL, "cc_graph_reorder: method must be CC_REORDER_SRC or CC_REORDER_LOWDEG");
@@ -97,6 +107,24 @@ extern "C" cc_status cc_graph_reorder(cc_graph* g, int method) {
     RCUDA(cub::DeviceRadixSort::SortPairs(tmp, tmp_bytes, k_in, k_out, v_in, v_out, (long long)m, 0,
                                           bits_for(n), s));
     RCUDA(cudaStreamSynchronize(s));
+    {
+        // the sorted pairs must be a permutation of the oriented input: check
+        // that every id is in range before the handle gathers with them
+        unsigned long long* d_bad = nullptr;
+        unsigned long long bad = 0;
+        RCUDA(cudaMalloc(&d_bad, sizeof bad));
+        RCUDA(cudaMemsetAsync(d_bad, 0, sizeof bad, s));
+        range_check_kernel<<<grid, 256, 0, s>>>(k_out, v_out, m, n, d_bad);
+        cudaError_t e2 = cudaGetLastError();
+        if (e2 == cudaSuccess) e2 = cudaMemcpyAsync(&bad, d_bad, sizeof bad, cudaMemcpyDeviceToHost, s);
+        if (e2 == cudaSuccess) e2 = cudaStreamSynchronize(s);
+        cudaFree(d_bad);
+        RCUDA(e2);
+        if (bad) {
+            st = cc::set_error(CC_ECUDA, "cc_graph_reorder: internal error, %llu reordered ids out of range", bad);
+            goto done;
+        }
+    }
     st = cc::graph_replace_edges(g, k_out, v_out);
     if (st == CC_OK) k_out = v_out = nullptr;  // now owned by the handle
 done:

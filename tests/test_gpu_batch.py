@@ -162,3 +162,29 @@ def test_batch_autotune_picks_valid_tuning(cc, mix):
     b2 = cc.cc_batch_init(vo, eo, s, d, autotune=1)
     assert cc.cc_batch_tuning(b2) == (budget, threads, ept)
     cc.cc_batch_free(b2)
+
+
+def test_batch_reorder_keeps_every_graph(cc, mix):
+    """cc_batch_reorder groups each graph's edges by its lower-degree endpoint;
+    labels, and in sync mode every sweep count, are unchanged."""
+    vo, eo, s, d, sh, dh, truth = mix
+    want_sweeps = []
+    for g in range(len(truth)):
+        a, bnd = int(eo[g]), int(eo[g + 1])
+        want_sweeps.append(oracle.contour_sync(int(vo[g + 1] - vo[g]), sh[a:bnd], dh[a:bnd], 2)[1])
+    # tune and solve first: the reorder must not depend on the plan's history
+    b = cc.cc_batch_init(vo, eo, s.clone(), d.clone(), autotune=1)
+    out = torch.empty(int(vo[-1]), dtype=torch.int32, device="cuda")
+    cc.cc_batch_run(b, out, 2, cc.CC_ASYNC, 1)
+    cc.cc_batch_reorder(b)
+    for tuning in TUNINGS:
+        if tuning is not None:
+            cc.cc_batch_set_tuning(b, *tuning)
+        for order, mode in [(2, 1), (0, 1), (4, 1)]:
+            out.fill_(-1)
+            cc.cc_batch_run(b, out, order, mode, 1)
+            _check_labels(vo, out, truth)
+        sweeps, _ = cc.cc_batch_run(b, out, 2, cc.CC_SYNC, 1)
+        assert sweeps.tolist() == want_sweeps
+        _check_labels(vo, out, truth)
+    cc.cc_batch_free(b)

@@ -62,7 +62,11 @@ def test_rmat_scale27_int64_edge_offsets(cc):
     got = out.cpu().numpy()
     out_full, _ = _solve(cc, g, n, 0, cc.CC_ASYNC)
     assert torch.equal(out, out_full)
+    cc.cc_graph_reorder(g, cc.CC_REORDER_LOWDEG)  # 2^31 pairs through the radix sort
+    out_r, _ = _solve(cc, g, n, 2, cc.CC_ASYNC)
+    assert torch.equal(out, out_r)
     cc.cc_free(g)
+    del out_r
     del out, out_full
     want = oracle.uf_labels(n, s.cpu().numpy(), d.cpu().numpy())
     assert np.array_equal(got, want)

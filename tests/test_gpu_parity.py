@@ -334,3 +334,32 @@ def test_generators_bit_identical_on_gpu():
     v2, e2, s2, d2, _ = gg.batch_mix(16, device="cuda", n_hi=2e4)
     assert torch.equal(v1, v2) and torch.equal(e1, e2)
     assert torch.equal(s1, s2.cpu()) and torch.equal(d1, d2.cpu())
+
+
+def test_non_default_streams_and_concurrent_handles(cc):
+    """Handles enqueue on the stream they were created with (or set later);
+    two handles on two streams run concurrently and stay correct."""
+    graphs = [SMALL["rmat12"](11), SMALL["grid64"](12)]
+    wants = [oracle.uf_labels(n, s, d) for n, s, d in graphs]
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    handles, outs, keep = [], [], []
+    for (n, s, d), st in zip(graphs, streams):
+        with torch.cuda.stream(st):
+            sg, dg = s.cuda(), d.cuda()
+            keep.append((sg, dg))
+            handles.append(cc.cc_init(n, sg, dg, stream=st.cuda_stream))
+            outs.append(torch.empty(n, dtype=torch.int32, device="cuda"))
+    for rep in range(3):
+        for h, o, st in zip(handles, outs, streams):
+            with torch.cuda.stream(st):
+                cc.cc_run(h, o, 0 if rep % 2 else 2, cc.CC_ASYNC, 1)
+    torch.cuda.synchronize()
+    for o, want in zip(outs, wants):
+        assert (o.cpu().numpy() == want).all()
+    cc.cc_graph_set_stream(handles[0], streams[1].cuda_stream)
+    with torch.cuda.stream(streams[1]):
+        cc.cc_run(handles[0], outs[0], 2, cc.CC_SYNC, 1)
+    torch.cuda.synchronize()
+    assert (outs[0].cpu().numpy() == wants[0]).all()
+    for h in handles:
+        cc.cc_free(h)
