@@ -6,7 +6,10 @@ log-uniform n in [1e3, 1e6]):
   2. time all 18 schedules (order {2, 4, full chain} x {sync, async} x check
      interval {1, 2, 4}) with cc_run, taking the faster of two device-timed
      runs each; every schedule returns identical labels;
-  3. label the graph with its fastest schedule.
+  3. label the graph with its fastest schedule; when several schedules are
+     within 3% of the fastest, the one with the smallest median time (relative
+     to each graph's best) over all training graphs is taken, so that
+     near-ties do not turn measurement noise into label noise.
 Then train the MLP on the GPU (cc_sched_train) and write the weight blob.
 
 Held-out evaluation: graphs drawn from another seed plus large R-MAT (up to
@@ -63,7 +66,7 @@ def time_schedules(n, s, d, reps=2):
 
 
 def build_training_set(n_graphs, chunk, log):
-    feats, labels, all_times = [], [], []
+    feats, all_times = [], []
     done = 0
     while done < n_graphs:
         cnt = min(chunk, n_graphs - done)
@@ -75,13 +78,22 @@ def build_training_set(n_graphs, chunk, log):
             a, b = int(eo[g]), int(eo[g + 1])
             t = time_schedules(int(vo[g + 1] - vo[g]), s[a:b], d[a:b])
             feats.append(F[g])
-            labels.append(int(np.argmin(t)))
             all_times.append(t)
         done += cnt
         del s, d
         torch.cuda.empty_cache()
         log(f"training graphs: {done}/{n_graphs}")
-    return np.array(feats, np.float32), np.array(labels, np.int32), np.array(all_times)
+    T = np.array(all_times)
+    return np.array(feats, np.float32), label_times(T), T
+
+
+def label_times(T, tol=1.03):
+    """Fastest schedule per row; near-ties broken by the global median ratio."""
+    ratio = T / T.min(axis=1, keepdims=True)
+    pref = np.argsort(np.argsort(np.median(ratio, axis=0)))  # rank of each schedule
+    near = ratio <= tol
+    score = np.where(near, pref[None, :], len(pref) + 1)
+    return np.argmin(score, axis=1).astype(np.int32)
 
 
 def heldout_graphs(n_mix):
