@@ -332,8 +332,15 @@ cc_status cc_graph_info(const cc_graph *g, int64_t *n, int64_t *m);
  * valid until cc_free or the next cc_graph_reorder. */
 cc_status cc_graph_edges(const cc_graph *g, const void **src, const void **dst);
 
-/* Release a handle and every device buffer it owns.  NULL is ignored. */
+/* Release a handle and every device buffer it owns.  NULL is ignored.  The
+ * release is enqueued on the handle's stream, which must still exist. */
 void cc_free(cc_graph *g);
+
+/* Device memory of graph handles comes from a per-device stream-ordered pool
+ * that keeps released memory for the next handle (repeated cc_init / cc_free
+ * cycles then cost no cudaMalloc/cudaFree).  This call waits for the device
+ * and returns all unused pool memory to it. */
+cc_status cc_release_memory(void);
 
 /* Static description of a status code. */
 const char *cc_strerror(cc_status s);

@@ -18,7 +18,7 @@ __all__ = [
     "CC_OK", "CC_EINVAL", "CC_EIDRANGE", "CC_ENOMEM", "CC_ECUDA", "CC_ENOTCONVERGED",
     "CC_ETIMEOUT", "CC_ID32", "CC_ID64", "CC_COO", "CC_CSR", "CC_SYNC", "CC_ASYNC",
     "CC_ORDER_FULL", "CC_ORDER_AUTO", "CC_ORDER_11MM", "CC_ORDER_1M1M", "CC_NOALLOC_MAX_N", "CCError", "cc_stats", "cc_graph", "lib", "LIB_PATH",
-    "cc_init", "cc_run", "cc_run_noalloc", "cc_free", "cc_batch_plan", "cc_batch_init",
+    "cc_init", "cc_run", "cc_run_noalloc", "cc_free", "cc_release_memory", "cc_batch_plan", "cc_batch_init",
     "cc_batch_run", "cc_batch_set_schedule", "cc_batch_run_scheduled", "cc_batch_tuning",
     "cc_batch_set_tuning", "cc_batch_reorder", "cc_batch_edges", "cc_batch_free", "cc_batch", "cc_sched_load", "cc_sched_blob_bytes",
     "cc_sched_param_count", "cc_sched_decode", "cc_graph_features", "cc_batch_features",
@@ -469,6 +469,15 @@ def cc_graph_info(g):
 
 def cc_graph_set_stream(g, stream):
     _check(lib.cc_graph_set_stream(g, int(stream)), "cc_graph_set_stream")
+
+
+lib.cc_release_memory.argtypes = []
+lib.cc_release_memory.restype = _int
+
+
+def cc_release_memory():
+    """Return the library's unused pooled device memory to the device."""
+    _check(lib.cc_release_memory(), "cc_release_memory")
 
 
 def cc_free(g):

@@ -76,7 +76,69 @@ int persistent_blocks(const void* fn, int threads, size_t smem) {
     return blocks;
 }
 
+// Device memory of handles comes from one stream-ordered pool per device
+// (cudaMallocFromPoolAsync / cudaFreeAsync) that keeps released memory for
+// reuse, so repeated cc_init / cc_free cycles do not pay for cudaMalloc and
+// cudaFree each time; cc_release_memory() returns it to the device.
+namespace {
+std::mutex g_pool_mu;
+cudaMemPool_t g_pools[64] = {};
+}  // namespace
+
+cudaError_t pool_for_device(cudaMemPool_t* out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_pool_mu);
+    if (!g_pools[dev]) {
+        cudaMemPoolProps props = {};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t p;
+        e = cudaMemPoolCreate(&p, &props);
+        if (e != cudaSuccess) return e;
+        unsigned long long keep = ~0ull;
+        e = cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &keep);
+        if (e != cudaSuccess) {
+            cudaMemPoolDestroy(p);
+            return e;
+        }
+        g_pools[dev] = p;
+    }
+    *out = g_pools[dev];
+    return cudaSuccess;
+}
+
+cudaError_t dmalloc(void** ptr, size_t bytes, cudaStream_t s) {
+    cudaMemPool_t pool;
+    cudaError_t e = pool_for_device(&pool);
+    if (e != cudaSuccess) return e;
+    return cudaMallocFromPoolAsync(ptr, bytes > 0 ? bytes : 16, pool, s);
+}
+
+cudaError_t dfree(void* ptr, cudaStream_t s) {
+    if (!ptr) return cudaSuccess;
+    return cudaFreeAsync(ptr, s);
+}
+
 }  // namespace cc
+
+extern "C" cc_status cc_release_memory(void) {
+    for (int d = 0; d < 64; ++d) {
+        cudaMemPool_t p = nullptr;
+        {
+            std::lock_guard<std::mutex> lock(cc::g_pool_mu);
+            p = cc::g_pools[d];
+        }
+        if (!p) continue;
+        cudaError_t e = cudaDeviceSynchronize();
+        if (e == cudaSuccess) e = cudaMemPoolTrimTo(p, 0);
+        if (e != cudaSuccess) return cc::cuda_fail(e, "cc_release_memory", __FILE__, __LINE__);
+    }
+    return CC_OK;
+}
 
 using cc::cuda_fail;
 using cc::set_error;
@@ -137,12 +199,12 @@ static void destroy(cc_graph* g) {
     free_loops(g);
     cc::sched_ctx_free(g->sched);
     if (g->own_edges) {
-        cudaFree(g->src);
-        cudaFree(g->dst);
+        cc::dfree(g->src, g->stream);
+        cc::dfree(g->dst, g->stream);
     }
-    cudaFree(g->L);
-    cudaFree(g->Lu);
-    cudaFree(g->ctl);
+    cc::dfree(g->L, g->stream);
+    cc::dfree(g->Lu, g->stream);
+    cc::dfree(g->ctl, g->stream);
     if (g->ctl_h) cudaFreeHost(g->ctl_h);
     if (g->cap) cudaStreamDestroy(g->cap);
     if (g->ev0) cudaEventDestroy(g->ev0);
@@ -324,8 +386,8 @@ static cc_status init_edges(cc_graph* g, int layout, const void* a, const void* 
     } else {
         g->own_edges = true;
         const size_t bytes = (size_t)(cnt > 0 ? cnt : 1) * B;
-        CC_CUDA(cudaMalloc(&g->src, bytes));
-        CC_CUDA(cudaMalloc(&g->dst, bytes));
+        CC_CUDA(cc::dmalloc(&g->src, bytes, s));
+        CC_CUDA(cc::dmalloc(&g->dst, bytes, s));
         const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
         if (layout == CC_COO) {
             if (cnt) {
@@ -335,7 +397,7 @@ static cc_status init_edges(cc_graph* g, int layout, const void* a, const void* 
         } else {
             // CSR: offsets (int64, n+1) and columns; rows are expanded on the device
             int64_t* off = nullptr;
-            CC_CUDA(cudaMalloc(&off, (size_t)(n + 1) * sizeof(int64_t)));
+            CC_CUDA(cc::dmalloc(reinterpret_cast<void**>(&off), (size_t)(n + 1) * sizeof(int64_t), s));
             cudaError_t e = cudaMemcpyAsync(off, a, (size_t)(n + 1) * sizeof(int64_t), kind, s);
             if (e == cudaSuccess && cnt) e = cudaMemcpyAsync(g->dst, b, cnt * B, kind, s);
             if (e == cudaSuccess) {
@@ -348,7 +410,7 @@ static cc_status init_edges(cc_graph* g, int layout, const void* a, const void* 
                 e = cudaStreamSynchronize(s);
             }
             if (e == cudaSuccess && g->ctl_h->bad_count) {
-                cudaFree(off);
+                cc::dfree(off, s);
                 return set_error(CC_EINVAL, "CSR offsets are not non-decreasing from 0 to nnz=%lld (first bad index %llu)",
                                  (long long)cnt, g->ctl_h->first_bad);
             }
@@ -358,7 +420,7 @@ static cc_status init_edges(cc_graph* g, int layout, const void* a, const void* 
                 e = cudaGetLastError();
             }
             if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-            cudaFree(off);
+            cc::dfree(off, s);
             if (e != cudaSuccess) return cuda_fail(e, "CSR expansion", __FILE__, __LINE__);
         }
     }
@@ -402,7 +464,7 @@ extern "C" cc_status cc_init(cc_graph** out, int64_t n, int id_bits, int layout,
         return x;
     };
     {
-        cudaError_t e = cudaMalloc(&g->ctl, sizeof(Ctl));
+        cudaError_t e = cc::dmalloc(reinterpret_cast<void**>(&g->ctl), sizeof(Ctl), s);
         if (e == cudaSuccess) e = cudaMallocHost(&g->ctl_h, sizeof(Ctl));
         if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&g->cap, cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaEventCreate(&g->ev0);
@@ -496,12 +558,12 @@ static cc_status run_impl(cc_graph* g, int order, int mode, int c, int32_t max_s
 
     void* L = labels_out;
     if (!out_on_device || (reinterpret_cast<uintptr_t>(labels_out) & 15)) {
-        if (!g->L) CC_CUDA(cudaMalloc(&g->L, g->n * B));
+        if (!g->L) CC_CUDA(cc::dmalloc(&g->L, g->n * B, s));
         L = g->L;
     }
     void* Lu = nullptr;
     if (mode == CC_SYNC) {
-        if (!g->Lu) CC_CUDA(cudaMalloc(&g->Lu, g->n * B));
+        if (!g->Lu) CC_CUDA(cc::dmalloc(&g->Lu, g->n * B, s));
         Lu = g->Lu;
     }
     cudaGraphExec_t loop = nullptr;
@@ -599,8 +661,8 @@ cc_status graph_replace_edges(cc_graph* g, void* src, void* dst) {
     sched_ctx_free(g->sched);
     g->sched = nullptr;
     if (g->own_edges) {
-        cudaFree(g->src);
-        cudaFree(g->dst);
+        dfree(g->src, g->stream);
+        dfree(g->dst, g->stream);
     }
     g->src = src;
     g->dst = dst;

@@ -22,6 +22,9 @@ void sched_ctx_free(SchedCtx* c);
 cc_status set_error(cc_status s, const char* fmt, ...);
 cc_status cuda_fail(cudaError_t e, const char* what, const char* file, int line);
 int device_sms();
+// Stream-ordered allocation from the library's per-device memory pool.
+cudaError_t dmalloc(void** ptr, size_t bytes, cudaStream_t s);
+cudaError_t dfree(void* ptr, cudaStream_t s);
 int persistent_blocks(const void* fn, int threads, size_t smem);
 
 // Graph accessors for the scheduler (features are computed on the graph's edges).

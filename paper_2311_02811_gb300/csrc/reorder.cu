@@ -86,12 +86,12 @@ extern "C" cc_status cc_graph_reorder(cc_graph* g, int method) {
     void* tmp = nullptr;
     size_t tmp_bytes = 0;
     const int grid = cc::device_sms() * 8;
-    RCUDA(cudaMalloc(&k_out, (size_t)m * sizeof(uint32_t)));
-    RCUDA(cudaMalloc(&v_out, (size_t)m * sizeof(uint32_t)));
+    RCUDA(cc::dmalloc(reinterpret_cast<void**>(&k_out), (size_t)m * sizeof(uint32_t), s));
+    RCUDA(cc::dmalloc(reinterpret_cast<void**>(&v_out), (size_t)m * sizeof(uint32_t), s));
     if (method == CC_REORDER_LOWDEG) {
-        RCUDA(cudaMalloc(&k_in, (size_t)m * sizeof(uint32_t)));
-        RCUDA(cudaMalloc(&v_in, (size_t)m * sizeof(uint32_t)));
-        RCUDA(cudaMalloc(&deg, (size_t)n * sizeof(int32_t)));
+        RCUDA(cc::dmalloc(reinterpret_cast<void**>(&k_in), (size_t)m * sizeof(uint32_t), s));
+        RCUDA(cc::dmalloc(reinterpret_cast<void**>(&v_in), (size_t)m * sizeof(uint32_t), s));
+        RCUDA(cc::dmalloc(reinterpret_cast<void**>(&deg), (size_t)n * sizeof(int32_t), s));
         RCUDA(cudaMemsetAsync(deg, 0, (size_t)n * sizeof(int32_t), s));
         degree_kernel<<<grid, 256, 0, s>>>(src, dst, m, deg);
         RCUDA(cudaGetLastError());
@@ -103,7 +103,7 @@ extern "C" cc_status cc_graph_reorder(cc_graph* g, int method) {
     }
     RCUDA(cub::DeviceRadixSort::SortPairs(nullptr, tmp_bytes, k_in, k_out, v_in, v_out, (long long)m, 0,
                                           bits_for(n), s));
-    RCUDA(cudaMalloc(&tmp, tmp_bytes));
+    RCUDA(cc::dmalloc(&tmp, tmp_bytes, s));
     RCUDA(cub::DeviceRadixSort::SortPairs(tmp, tmp_bytes, k_in, k_out, v_in, v_out, (long long)m, 0,
                                           bits_for(n), s));
     RCUDA(cudaStreamSynchronize(s));
@@ -112,13 +112,13 @@ extern "C" cc_status cc_graph_reorder(cc_graph* g, int method) {
         // that every id is in range before the handle gathers with them
         unsigned long long* d_bad = nullptr;
         unsigned long long bad = 0;
-        RCUDA(cudaMalloc(&d_bad, sizeof bad));
+        RCUDA(cc::dmalloc(reinterpret_cast<void**>(&d_bad), sizeof bad, s));
         RCUDA(cudaMemsetAsync(d_bad, 0, sizeof bad, s));
         range_check_kernel<<<grid, 256, 0, s>>>(k_out, v_out, m, n, d_bad);
         cudaError_t e2 = cudaGetLastError();
         if (e2 == cudaSuccess) e2 = cudaMemcpyAsync(&bad, d_bad, sizeof bad, cudaMemcpyDeviceToHost, s);
         if (e2 == cudaSuccess) e2 = cudaStreamSynchronize(s);
-        cudaFree(d_bad);
+        cc::dfree(d_bad, s);
         RCUDA(e2);
         if (bad) {
             st = cc::set_error(CC_ECUDA, "cc_graph_reorder: internal error, %llu reordered ids out of range", bad);
@@ -129,12 +129,12 @@ extern "C" cc_status cc_graph_reorder(cc_graph* g, int method) {
     if (st == CC_OK) k_out = v_out = nullptr;  // now owned by the handle
 done:
     if (method == CC_REORDER_LOWDEG) {
-        cudaFree(k_in);
-        cudaFree(v_in);
+        cc::dfree(k_in, s);
+        cc::dfree(v_in, s);
     }
-    cudaFree(deg);
-    cudaFree(tmp);
-    cudaFree(k_out);
-    cudaFree(v_out);
+    cc::dfree(deg, s);
+    cc::dfree(tmp, s);
+    cc::dfree(k_out, s);
+    cc::dfree(v_out, s);
     return st;
 }

@@ -21,6 +21,7 @@
 // training mean/std; weights BF16, biases and accumulation FP32.
 // Output class k = order_idx * 6 + async * 3 + interval_idx with orders
 // {2, 4, full chain} and intervals {1, 2, 4}.
+#include <cooperative_groups.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -140,14 +141,26 @@ __global__ void __launch_bounds__(kFeatThreads) features_kernel(FeatArgs a) {
         if (threadIdx.x < 8) s_ecc[threadIdx.x] = 0;
         __syncthreads();
         // sample edges -> slots; degrees on the sample
-        for (long long j = threadIdx.x; j < S; j += blockDim.x) {
-            const long long e = e0 + sample_pos(j, m, S);
-            const int32_t pu = table_slot(keys, a.src[e], owned, &s_owned);
-            const int32_t pv = table_slot(keys, a.dst[e], owned, &s_owned);
-            su[j] = pu;
-            sv[j] = pv;
-            atomicAdd(deg + pu, 1);
-            atomicAdd(deg + pv, 1);
+        for (long long j0 = threadIdx.x; j0 < S; j0 += (long long)blockDim.x * 4) {
+            int32_t eu[4], ev[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const long long j = j0 + (long long)k * blockDim.x;
+                const long long e = e0 + sample_pos(j < S ? j : 0, m, S);
+                eu[k] = a.src[e];
+                ev[k] = a.dst[e];
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const long long j = j0 + (long long)k * blockDim.x;
+                if (j >= S) continue;
+                const int32_t pu = table_slot(keys, eu[k], owned, &s_owned);
+                const int32_t pv = table_slot(keys, ev[k], owned, &s_owned);
+                su[j] = pu;
+                sv[j] = pv;
+                atomicAdd(deg + pu, 1);
+                atomicAdd(deg + pv, 1);
+            }
         }
         __syncthreads();
         const int32_t no = s_owned;
@@ -166,26 +179,55 @@ __global__ void __launch_bounds__(kFeatThreads) features_kernel(FeatArgs a) {
             atomicOr(word + su[j], (1u << threadIdx.x) | (1u << (8 + threadIdx.x)));
         }
         __syncthreads();
+        // Level-synchronous BFS; each thread takes 4 items per step and issues
+        // all their loads before any atomic so that the latencies overlap.
+        constexpr int U = 4;
         for (int level = 1; level <= kLevels; ++level) {
-            for (long long j = threadIdx.x; j < S; j += blockDim.x) {
-                const int32_t pu = su[j], pv = sv[j];
-                const uint32_t wu = word[pu], wv = word[pv];
-                const uint32_t to_v = ((wu >> 8) & 0xffu) & ~(wv & 0xffu);
-                const uint32_t to_u = ((wv >> 8) & 0xffu) & ~(wu & 0xffu);
-                if (to_v) atomicOr(word + pv, to_v << 16);
-                if (to_u) atomicOr(word + pu, to_u << 16);
+            for (long long j0 = threadIdx.x; j0 < S; j0 += (long long)blockDim.x * U) {
+                int32_t pu[U], pv[U];
+                uint32_t wu[U], wv[U];
+#pragma unroll
+                for (int k = 0; k < U; ++k) {
+                    const long long j = j0 + (long long)k * blockDim.x;
+                    pu[k] = j < S ? su[j] : -1;
+                    pv[k] = j < S ? sv[j] : -1;
+                }
+#pragma unroll
+                for (int k = 0; k < U; ++k) {
+                    wu[k] = pu[k] >= 0 ? word[pu[k]] : 0u;
+                    wv[k] = pv[k] >= 0 ? word[pv[k]] : 0u;
+                }
+#pragma unroll
+                for (int k = 0; k < U; ++k) {
+                    if (pu[k] < 0) continue;
+                    const uint32_t to_v = ((wu[k] >> 8) & 0xffu) & ~(wv[k] & 0xffu);
+                    const uint32_t to_u = ((wv[k] >> 8) & 0xffu) & ~(wu[k] & 0xffu);
+                    if (to_v) atomicOr(word + pv[k], to_v << 16);
+                    if (to_u) atomicOr(word + pu[k], to_u << 16);
+                }
             }
             __syncthreads();
             int any = 0;
-            for (int32_t i = threadIdx.x; i < no; i += blockDim.x) {
-                const int32_t x = owned[i];
-                const uint32_t w = word[x];
-                const uint32_t fresh = ((w >> 16) & 0xffu) & ~(w & 0xffu);
-                word[x] = (w & 0xffu) | fresh | (fresh << 8);
-                if (fresh) {
-                    any = 1;
-                    for (int b = 0; b < 8; ++b)
-                        if (fresh >> b & 1u) atomicMax(&s_ecc[b], level);
+            for (int32_t i0 = threadIdx.x; i0 < no; i0 += blockDim.x * U) {
+                int32_t x[U];
+                uint32_t w[U];
+#pragma unroll
+                for (int k = 0; k < U; ++k) {
+                    const int32_t i = i0 + k * blockDim.x;
+                    x[k] = i < no ? owned[i] : -1;
+                }
+#pragma unroll
+                for (int k = 0; k < U; ++k) w[k] = x[k] >= 0 ? word[x[k]] : 0u;
+#pragma unroll
+                for (int k = 0; k < U; ++k) {
+                    if (x[k] < 0) continue;
+                    const uint32_t fresh = ((w[k] >> 16) & 0xffu) & ~(w[k] & 0xffu);
+                    word[x[k]] = (w[k] & 0xffu) | fresh | (fresh << 8);
+                    if (fresh) {
+                        any = 1;
+                        for (int b = 0; b < 8; ++b)
+                            if (fresh >> b & 1u) atomicMax(&s_ecc[b], level);
+                    }
                 }
             }
             if (__syncthreads_or(any) == 0) break;
@@ -212,6 +254,161 @@ __global__ void __launch_bounds__(kFeatThreads) features_kernel(FeatArgs a) {
             for (int b = 0; b < 8; ++b) f[4 + b] = (float)log2(1.0 + (double)s_ecc[b]);
         }
         __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// features of ONE graph on a thread-block cluster of 8 CTAs (8 SMs)
+// ---------------------------------------------------------------------------
+//
+// Same definition as features_kernel, computed with the vertex table spread
+// over the shared memory of the 8 CTAs of a cluster (distributed shared
+// memory): a vertex's slot lives in CTA (hash >> 29), each CTA takes 1/8 of
+// the sample edges, and remote slots are read and updated with DSMEM loads
+// and atomics.  Phases and BFS levels are separated by cluster barriers.
+
+namespace cgx = cooperative_groups;
+
+constexpr int kCl = 8;                         // CTAs per cluster
+constexpr int kPart = kSlots / kCl;            // slots per CTA
+constexpr int kClEdges = kSample / kCl;        // sample edges per CTA
+static_assert((kPart & (kPart - 1)) == 0, "slot partition must be a power of two");
+constexpr int kPartBits = 13;
+static_assert((1 << kPartBits) == kPart, "kPartBits");
+
+struct ClusterSmem {
+    int32_t keys[kPart];
+    int32_t deg[kPart];
+    uint32_t word[kPart];
+    int32_t owned[kPart];   // local slots in use
+    int32_t su[kClEdges];   // global slot id (owner << kPartBits | local) of this CTA's edges
+    int32_t sv[kClEdges];
+    int32_t n_owned;
+    int32_t maxdeg;                     // rank-0 accumulators
+    unsigned long long sumsq;
+    int32_t ecc[8];
+    int32_t any[kLevels + 2];
+};
+
+__device__ __forceinline__ int32_t cl_slot(cgx::cluster_group& cl, ClusterSmem* me, int32_t x) {
+    const uint32_t h = (uint32_t)x * 2654435761u;
+    const int owner = (int)(h >> 29);
+    uint32_t loc = (h >> 13) & (kPart - 1);
+    ClusterSmem* o = cl.map_shared_rank(me, owner);
+    for (int probe = 0; probe < kPart; ++probe) {
+        const int32_t k = atomicCAS(&o->keys[loc], -1, x);
+        if (k == -1) {
+            o->owned[atomicAdd(&o->n_owned, 1)] = (int32_t)loc;
+            return (owner << kPartBits) | (int32_t)loc;
+        }
+        if (k == x) return (owner << kPartBits) | (int32_t)loc;
+        loc = (loc + 1) & (kPart - 1);
+    }
+    return -1;  // unreachable: at most 2 * kSample vertices in 8 * kPart slots
+}
+
+__device__ __forceinline__ uint32_t* cl_word(cgx::cluster_group& cl, ClusterSmem* me, int32_t slot) {
+    return &cl.map_shared_rank(me, slot >> kPartBits)->word[slot & (kPart - 1)];
+}
+
+__global__ void __launch_bounds__(kFeatThreads) features_cluster_kernel(const int64_t* off_v, const int64_t* off_e,
+                                                                     const int32_t* src, const int32_t* dst,
+                                                                     float* out) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    ClusterSmem* me = reinterpret_cast<ClusterSmem*>(smem_raw);
+    cgx::cluster_group cl = cgx::this_cluster();
+    const int rank = (int)cl.block_rank();
+    ClusterSmem* r0 = cl.map_shared_rank(me, 0);
+    const long long n = off_v[1] - off_v[0];
+    const long long e0 = off_e[0];
+    const long long m = off_e[1] - e0;
+    const long long S = m < kSample ? m : kSample;
+    const long long per = (S + kCl - 1) / kCl;
+    const long long jb = rank * per;
+    const long long je = min(S, jb + per);
+    for (int i = threadIdx.x; i < kPart; i += blockDim.x) {
+        me->keys[i] = -1;
+        me->deg[i] = 0;
+        me->word[i] = 0;
+    }
+    if (threadIdx.x == 0) {
+        me->n_owned = 0;
+        me->maxdeg = 0;
+        me->sumsq = 0;
+    }
+    if (threadIdx.x < 8) me->ecc[threadIdx.x] = 0;
+    if (threadIdx.x < kLevels + 2) me->any[threadIdx.x] = 0;
+    cl.sync();
+    // this CTA's share of the sample: slots and degrees
+    for (long long j = jb + threadIdx.x; j < je; j += blockDim.x) {
+        const long long e = e0 + sample_pos(j, m, S);
+        const int32_t pu = cl_slot(cl, me, src[e]);
+        const int32_t pv = cl_slot(cl, me, dst[e]);
+        me->su[j - jb] = pu;
+        me->sv[j - jb] = pv;
+        atomicAdd(&cl.map_shared_rank(me, pu >> kPartBits)->deg[pu & (kPart - 1)], 1);
+        atomicAdd(&cl.map_shared_rank(me, pv >> kPartBits)->deg[pv & (kPart - 1)], 1);
+    }
+    cl.sync();
+    {
+        unsigned long long sq = 0;
+        int32_t mx = 0;
+        for (int32_t i = threadIdx.x; i < me->n_owned; i += blockDim.x) {
+            const long long dd = me->deg[me->owned[i]];
+            sq += (unsigned long long)(dd * dd);
+            mx = max(mx, (int32_t)dd);
+        }
+        if (sq) atomicAdd(&r0->sumsq, sq);
+        if (mx) atomicMax(&r0->maxdeg, mx);
+    }
+    // the 8 BFS sources: src endpoints of sample positions floor((2i+1) S / 16)
+    if (threadIdx.x < 8 && S > 0) {
+        const long long j = ((2ll * threadIdx.x + 1) * S) / 16;
+        if (j >= jb && j < je)
+            atomicOr(cl_word(cl, me, me->su[j - jb]), (1u << threadIdx.x) | (1u << (8 + threadIdx.x)));
+    }
+    cl.sync();
+    for (int level = 1; level <= kLevels; ++level) {
+        for (long long j = jb + threadIdx.x; j < je; j += blockDim.x) {
+            const int32_t pu = me->su[j - jb], pv = me->sv[j - jb];
+            uint32_t* au = cl_word(cl, me, pu);
+            uint32_t* av = cl_word(cl, me, pv);
+            const uint32_t wu = *au, wv = *av;
+            const uint32_t to_v = ((wu >> 8) & 0xffu) & ~(wv & 0xffu);
+            const uint32_t to_u = ((wv >> 8) & 0xffu) & ~(wu & 0xffu);
+            if (to_v) atomicOr(av, to_v << 16);
+            if (to_u) atomicOr(au, to_u << 16);
+        }
+        cl.sync();
+        int any = 0;
+        for (int32_t i = threadIdx.x; i < me->n_owned; i += blockDim.x) {
+            const int32_t x = me->owned[i];
+            const uint32_t w = me->word[x];
+            const uint32_t fresh = ((w >> 16) & 0xffu) & ~(w & 0xffu);
+            me->word[x] = (w & 0xffu) | fresh | (fresh << 8);
+            if (fresh) {
+                any = 1;
+                for (int b = 0; b < 8; ++b)
+                    if (fresh >> b & 1u) atomicMax(&r0->ecc[b], level);
+            }
+        }
+        if (any) atomicOr(&r0->any[level], 1);
+        cl.sync();
+        if (r0->any[level] == 0) break;
+    }
+    cl.sync();
+    if (rank == 0 && threadIdx.x == 0) {
+        const double scale = S > 0 ? (double)m / (double)S : 0.0;
+        const double nn = n > 0 ? (double)n : 1.0;
+        const double mean = 2.0 * (double)S / nn;
+        const double var_s = (double)me->sumsq / nn - mean * mean;
+        const double var_est = (var_s > 0 ? var_s : 0.0) * scale * scale;
+        const double max_est = (double)me->maxdeg * scale;
+        out[0] = (float)log2(1.0 + (double)n);
+        out[1] = (float)log2(1.0 + (double)m);
+        out[2] = (float)log2(1.0 + var_est);
+        out[3] = (float)log2(1.0 + max_est);
+        for (int b = 0; b < 8; ++b) out[4 + b] = (float)log2(1.0 + (double)me->ecc[b]);
     }
 }
 
@@ -439,14 +636,18 @@ struct SchedCtx {
     float* d_feat = nullptr;   // G x kFeat
     int32_t* d_cls = nullptr;  // G
     std::vector<int32_t> h_cls;  // host copy of the classes
+    std::vector<int64_t> h_off;  // offsets, re-sent before each use when shared
     long long version = -1;    // model version h_cls was computed with
+    bool shared = false;       // device buffers belong to the process (G == 1)
 };
 
 void sched_ctx_free(SchedCtx* c) {
     if (!c) return;
-    cudaFree(c->d_off);
-    cudaFree(c->d_feat);
-    cudaFree(c->d_cls);
+    if (!c->shared) {
+        cudaFree(c->d_off);
+        cudaFree(c->d_feat);
+        cudaFree(c->d_cls);
+    }
     delete c;
 }
 
@@ -489,11 +690,36 @@ cc_status scratch_get(int ctas, cudaStream_t s) {
     return CC_OK;
 }
 
+// Device buffers shared by every single-graph context (used under g_mu).
+int64_t* g_one_off = nullptr;
+float* g_one_feat = nullptr;
+int32_t* g_one_cls = nullptr;
+
 cc_status ctx_get(cc::SchedCtx** slot, int32_t G, const int64_t* off_v, const int64_t* off_e, cudaStream_t s) {
     if (*slot) return CC_OK;
     cc::SchedCtx* c = new (std::nothrow) cc::SchedCtx();
     if (!c) return cc::set_error(CC_ENOMEM, "scheduler context");
     c->G = G;
+    if (G == 1) {
+        // a handle has one graph: no allocation of its own
+        if (!g_one_off) {
+            cudaError_t e = cudaMalloc(&g_one_off, 4 * sizeof(int64_t));
+            if (e == cudaSuccess) e = cudaMalloc(&g_one_feat, kFeat * sizeof(float));
+            if (e == cudaSuccess) e = cudaMalloc(&g_one_cls, 4 * sizeof(int32_t));
+            if (e != cudaSuccess) {
+                delete c;
+                return cc::cuda_fail(e, "scheduler buffers", __FILE__, __LINE__);
+            }
+        }
+        c->shared = true;
+        c->d_off = g_one_off;
+        c->d_feat = g_one_feat;
+        c->d_cls = g_one_cls;
+        c->h_cls.assign(1, 0);
+        c->h_off = {off_v[0], off_v[1], off_e[0], off_e[1]};
+        *slot = c;
+        return CC_OK;
+    }
     cudaError_t e = cudaMalloc(&c->d_off, 2 * (size_t)(G + 1) * sizeof(int64_t));
     if (e == cudaSuccess) e = cudaMalloc(&c->d_feat, (size_t)std::max(G, 1) * kFeat * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc(&c->d_cls, (size_t)std::max(G, 1) * sizeof(int32_t));
@@ -513,6 +739,30 @@ cc_status ctx_get(cc::SchedCtx** slot, int32_t G, const int64_t* off_v, const in
 // Features of every graph of the context into c->d_feat (caller holds g_mu).
 cc_status run_features(cc::SchedCtx* c, const int32_t* src, const int32_t* dst, cudaStream_t s) {
     if (c->G == 0) return CC_OK;
+    if (c->G == 1) {  // one graph: a cluster of 8 CTAs
+        SCUDA(cudaMemcpyAsync(c->d_off, c->h_off.data(), 4 * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+        static bool attr_set = false;
+        if (!attr_set) {
+            SCUDA(cudaFuncSetAttribute(features_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)sizeof(ClusterSmem)));
+            attr_set = true;
+        }
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(kCl, 1, 1);
+        cfg.blockDim = dim3(kFeatThreads, 1, 1);
+        cfg.dynamicSmemBytes = sizeof(ClusterSmem);
+        cfg.stream = s;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = kCl;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        SCUDA(cudaLaunchKernelEx(&cfg, features_cluster_kernel, (const int64_t*)c->d_off,
+                                 (const int64_t*)(c->d_off + 2), src, dst, c->d_feat));
+        return CC_OK;
+    }
     const int grid = std::max(1, std::min<int>(c->G, cc::device_sms() * 2));
     cc_status st = scratch_get(grid, s);
     if (st != CC_OK) return st;

@@ -72,3 +72,8 @@ def test_scheduler_host_side_without_gpu(built_lib):
         cc.cc_sched_decode(18)
     assert cc.lib.cc_sched_load(b"not a blob", 10) == cc.CC_EINVAL
     assert cc.cc_sched_blob_bytes() == 120 + 2 * (64 * 12 + 64 * 64 * 2 + 18 * 64) + 4 * (64 * 3 + 18)
+
+
+def test_release_memory_without_pools(built_lib):
+    import paper_2311_02811_gb300 as cc
+    cc.cc_release_memory()  # nothing allocated yet: no CUDA call is made
