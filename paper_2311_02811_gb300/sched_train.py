@@ -165,6 +165,8 @@ def main():
     ap.add_argument("--out", default=os.path.join(HERE, "sched_weights.bin"))
     ap.add_argument("--report", default=os.path.join(HERE, "sched_weights.json"))
     ap.add_argument("--dump", default="", help="also save features, labels and timings (.npz)")
+    ap.add_argument("--eval-only", action="store_true",
+                    help="evaluate the weights in --out on the held-out set and update the report")
     args = ap.parse_args()
     t0 = time.time()
 
@@ -172,6 +174,21 @@ def main():
         print(f"[{time.time() - t0:7.1f}s] {msg}", flush=True)
 
     torch.cuda.set_device(0)
+    if args.eval_only:
+        with open(args.out, "rb") as f:
+            cc.cc_sched_load(f.read())
+        rows, tot = evaluate(args.heldout, log)
+        report = json.load(open(args.report)) if os.path.exists(args.report) else {}
+        report.update({"heldout_totals_ms": tot,
+                       "heldout_speedup_vs_plain": tot["plain_ms"] / tot["learned_ms"],
+                       "heldout_speedup_vs_c2": tot["c2_ms"] / tot["learned_ms"],
+                       "heldout_first_call_speedup_vs_plain": tot["plain_first_ms"] / tot["learned_first_ms"],
+                       "heldout_first_call_speedup_vs_c2": tot["c2_first_ms"] / tot["learned_first_ms"],
+                       "heldout_all_identical": all(r["identical"] for r in rows), "heldout": rows})
+        with open(args.report, "w") as f:
+            json.dump(report, f, indent=0, separators=(",", ":"))
+        log(f"updated {args.report}")
+        return
     X, y, T = build_training_set(args.train, args.chunk, log)
     if args.dump:
         np.savez_compressed(args.dump, X=X, y=y, T=T)
@@ -201,7 +218,7 @@ def main():
               "heldout_all_identical": all(r["identical"] for r in rows),
               "heldout": rows}
     with open(args.report, "w") as f:
-        json.dump(report, f, indent=1)
+        json.dump(report, f, indent=0, separators=(",", ":"))
     log(f"wrote {args.out} and {args.report}")
 
 
