@@ -17,6 +17,10 @@ Contents (each function cites the passage of the paper it follows):
                         of Def. 3 (``contour_sim.c``), returning every
                         per-iteration state of L.
 * ``degree_features``-- plain-definition graph statistics for the scheduler.
+* ``omp_contour``    -- multicore asynchronous Contour (C-1, C-2, C-m) with
+                        OpenMP (``contour_omp.c``, Section III-B): not a
+                        checker but the timed multicore CPU baseline; pinned
+                        against ``uf_labels`` like the GPU path.
 
 All three labellers are pinned in ``tests/test_oracle.py`` against brute-force
 reachability, closed forms and the iteration bounds of Lemma 2 / the Theorem.
@@ -32,7 +36,10 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB_PATH = os.path.join(_HERE, "liboracle.so")
 _SOURCES = ["uf.c", "contour_sim.c"]
+_OMP_LIB_PATH = os.path.join(_HERE, "liboracle_omp.so")
+_OMP_SOURCES = ["contour_omp.c"]
 _lib = None
+_omp_lib = None
 
 
 def build(force: bool = False) -> str:
@@ -46,6 +53,20 @@ def build(force: bool = False) -> str:
     subprocess.check_call(["gcc", "-O2", "-std=c99", "-shared", "-fPIC", "-o", tmp, *srcs])
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
+
+
+def build_omp(force: bool = False) -> str:
+    """Compile the multicore baseline into ``oracle/liboracle_omp.so``
+    (gcc -fopenmp).  Raises ``subprocess.CalledProcessError`` when the host
+    compiler has no OpenMP."""
+    srcs = [os.path.join(_HERE, s) for s in _OMP_SOURCES]
+    if not force and os.path.exists(_OMP_LIB_PATH):
+        if os.path.getmtime(_OMP_LIB_PATH) >= max(os.path.getmtime(s) for s in srcs):
+            return _OMP_LIB_PATH
+    tmp = _OMP_LIB_PATH + f".tmp{os.getpid()}"
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-fopenmp", "-shared", "-fPIC", "-o", tmp, *srcs])
+    os.replace(tmp, _OMP_LIB_PATH)
+    return _OMP_LIB_PATH
 
 
 def _load():
@@ -152,6 +173,33 @@ def contour_sync(n: int, src, dst, order: int = 2, max_iters: int = 10_000,
     if record:
         states = states[:iters].copy()
     return L, iters, converged, states
+
+
+def omp_contour(n: int, src, dst, order: int = 2, threads: int = 0, max_iters: int = 1 << 20):
+    """Asynchronous order-h Contour on the host's cores (``contour_omp.c``).
+
+    Returns ``(labels, iterations, threads_used)``; raises RuntimeError when
+    ``max_iters`` iterations do not reach the fixed point.
+    """
+    global _omp_lib
+    if _omp_lib is None:
+        build_omp()
+        lib = ctypes.CDLL(_OMP_LIB_PATH)
+        i64, i32, p = ctypes.c_int64, ctypes.c_int32, ctypes.c_void_p
+        lib.omp_contour_async_i32.argtypes = [i64, i64, p, p, i32, i64, i32, p, p]
+        lib.omp_contour_async_i32.restype = i64
+        _omp_lib = lib
+    s, d = _as_np(src, np.int32), _as_np(dst, np.int32)
+    assert s.shape == d.shape
+    if s.size and (min(s.min(), d.min()) < 0 or max(s.max(), d.max()) >= n):
+        raise OracleIdError(-1)
+    L = np.empty(n, dtype=np.int32)
+    used = ctypes.c_int32(0)
+    it = _omp_lib.omp_contour_async_i32(n, s.size, s.ctypes.data, d.ctypes.data, int(order), int(max_iters),
+                                        int(threads), L.ctypes.data, ctypes.byref(used))
+    if it < 0:
+        raise RuntimeError(f"omp_contour: no fixed point after {max_iters} iterations")
+    return L, int(it), int(used.value)
 
 
 def degree_features(n: int, src, dst) -> dict:

@@ -306,3 +306,54 @@ def test_degree_features_plain(oracle_lib):
     # degrees: 0->2, 1->2, 2->4 (self-loop counts twice), 3->0
     assert f["m"] == 4 and f["deg_max"] == 4.0
     assert f["deg_mean"] == 2.0 and f["deg_var"] == 2.0
+
+
+# ---------------------------------------------------------------------------
+# the multicore asynchronous Contour baseline (contour_omp.c)
+# ---------------------------------------------------------------------------
+
+def _omp_graphs():
+    yield "path", 5000, *gg.path(5000, seed=11)
+    yield "grid", 64 * 64, *gg.grid(64, 64, seed=12)
+    yield "rmat12", 1 << 12, *gg.rmat(12, seed=13)
+    n64, s64, d64 = gg.components64()
+    yield "components64", n64, s64, d64
+    yield "er", 3000, *gg.er(3000, 2000, seed=14)
+
+
+@pytest.mark.parametrize("threads", [1, 4])
+@pytest.mark.parametrize("order", [1, 2, 1024])
+def test_omp_contour_matches_union_find(order, threads):
+    for name, n, s, d in _omp_graphs():
+        got, iters, used = oracle.omp_contour(n, s, d, order=order, threads=threads)
+        assert np.array_equal(got, oracle.uf_labels(n, s, d)), (name, order, threads)
+        assert used == threads and iters >= 1
+
+
+def test_omp_contour_in_place_updates():
+    """In-place (asynchronous) updates, Section III-B1: one thread over the
+    sorted path 0-1, 1-2, ... in increasing order carries label 0 to the end
+    within the first iteration (each edge reads the label its predecessor has
+    just written), so the second iteration changes nothing.  The synchronous
+    Alg. 1 needs about log_1.5(n) iterations on the same input."""
+    n = 1000
+    s = np.arange(n - 1, dtype=np.int32)
+    d = s + 1
+    for order in (1, 2, 1024):
+        got, iters, _ = oracle.omp_contour(n, s, d, order=order, threads=1)
+        assert iters == 2 and not got.any()
+    _, sync_iters, _, _ = oracle.contour_sync(n, s, d, 2)
+    assert sync_iters > 10
+    # reversed order: order 1 moves label 0 one vertex per iteration
+    got, iters, _ = oracle.omp_contour(n, s[::-1].copy(), d[::-1].copy(), order=1, threads=1)
+    assert not got.any() and iters == n
+
+
+def test_omp_contour_edge_cases():
+    assert oracle.omp_contour(0, [], [], threads=2)[0].size == 0
+    got, iters, _ = oracle.omp_contour(5, [], [], threads=2)
+    assert got.tolist() == [0, 1, 2, 3, 4] and iters == 1
+    got, _, _ = oracle.omp_contour(4, [3, 2, 2], [3, 2, 0], threads=2)
+    assert got.tolist() == [0, 1, 0, 3]
+    with pytest.raises(oracle.OracleIdError):
+        oracle.omp_contour(3, [0], [3])
