@@ -49,7 +49,9 @@ def parse():
     p.add_argument("--cpu-seconds", type=float, default=12.0)
     p.add_argument("--batch-graphs", type=int, default=1024,
                    help="also compare batched + learned vs plain on a batch-mix of this many graphs (0: off)")
-    p.add_argument("--reorder", choices=["none", "src", "lowdeg"], default="lowdeg",
+    p.add_argument("--launch", choices=["graph", "host"], default="graph",
+                   help="sweep loop as a conditional CUDA graph, or host-polled blocks (for profilers)")
+    p.add_argument("--reorder", choices=["none", "src", "lowdeg", "hub"], default="lowdeg",
                    help="cc_graph_reorder layout step once before timing (included in e2e)")
     p.add_argument("--entry", choices=["cc_run", "noalloc"], default="cc_run",
                    help="cc_run (conditional CUDA-graph loop) or cc_run_noalloc (host-polled "
@@ -306,12 +308,17 @@ def run_ours(args, rank, world, local):
     m = s.numel()
     stream = torch.cuda.current_stream()
     g = cc.cc_init(n, s, d, stream=stream.cuda_stream)
-    reorder = {"none": 0, "src": cc.CC_REORDER_SRC, "lowdeg": cc.CC_REORDER_LOWDEG}[args.reorder]
+    reorder = {"none": 0, "src": cc.CC_REORDER_SRC, "lowdeg": cc.CC_REORDER_LOWDEG,
+               "hub": cc.CC_REORDER_HUB}[args.reorder]
+    if reorder == cc.CC_REORDER_HUB and args.entry == "noalloc":
+        raise SystemExit("--entry noalloc takes plain edge lists; hub-encoded edges need cc_run")
     reorder_ms = None
     if reorder:
         t0 = time.perf_counter()
         cc.cc_graph_reorder(g, reorder)
         reorder_ms = 1e3 * (time.perf_counter() - t0)
+    if args.launch == "host":
+        cc.cc_graph_set_launch(g, cc.CC_LAUNCH_HOST)
     out = torch.empty(n, dtype=torch.int32, device=dev)
     # the no-alloc entry runs the same sweep kernel on the handle's (possibly
     # reordered) edge arrays with host-polled plain launches
@@ -346,6 +353,7 @@ def run_ours(args, rank, world, local):
         "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "int32", "data": "synthetic",
         "config": dict(cfg, n=n, m=m, order=args.order, mode=args.mode, check_interval=args.interval,
+                       sweep_loop=("conditional CUDA graph" if args.launch == "graph" else "host-polled blocks"),
                        ids="int32", parallelism=f"replicas x{world}" if world > 1 else "single GPU",
                        l2="inputs larger than L2: edge list %.2f GB streamed every sweep" % (8 * m / 1e9),
                        edge_order=("as generated (shuffled)" if not reorder else
@@ -368,7 +376,7 @@ def run_ours(args, rank, world, local):
             line["e2e_without_reorder"] = e2e(cc, n, s, d, args, mode, world, stream, 0)
 
     if not args.no_variants and rank == 0:
-        line["variants"] = variants(cc, g, out, n, m, args, dev, seed, stream)
+        line["variants"] = variants(cc, g, out, n, m, args, dev, seed, stream, s, d)
     if args.batch_graphs > 0 and rank == 0:
         line["batch"] = batch_compare(cc, args.batch_graphs, args, dev, stream, gg.BASE_SEED + 3)
 
@@ -417,7 +425,7 @@ def e2e(cc, n, s, d, args, mode, world, stream, reorder=0):
             "ms_per_step": ms / steps}
 
 
-def variants(cc, g, out, n, m, args, dev, seed, stream):
+def variants(cc, g, out, n, m, args, dev, seed, stream, s=None, d=None):
     res = {}
 
     def measure(gh, o, nn, mm, order, mode, c, reps=3):
@@ -438,6 +446,22 @@ def variants(cc, g, out, n, m, args, dev, seed, stream):
         r["schedule"] = [st.order, st.mode, st.check_interval]
         res[f"{args.workload}/learned"] = r
         cc.cc_sched_load(None)
+    if s is not None and args.workload.startswith("rmat"):
+        # the same graph kept as CSR (native row walk, no edge-list expansion):
+        # each edge once in its src row, and stored in both rows (symmetric)
+        for sym, name in [(False, "csr"), (True, "csr-sym")]:
+            off, cols = gg.to_csr(n, s, d, symmetric=sym)
+            layout = cc.CC_CSR_NATIVE_SYM if sym else cc.CC_CSR_NATIVE
+            gc = cc.cc_init(n, off, cols, m=cols.numel(), id_bits=32, layout=layout, on_device=True,
+                            stream=stream.cuda_stream)
+            for order, mode, oname in [(2, cc.CC_ASYNC, "o2-async"), (0, cc.CC_ASYNC, "full-async"),
+                                       (2, cc.CC_SYNC, "o2-sync")]:
+                r = measure(gc, out, n, m, order, mode, 1)
+                r["entries"] = int(cols.numel())
+                res[f"{args.workload}-{name}/{oname}"] = r
+            cc.cc_free(gc)
+            del off, cols
+            torch.cuda.empty_cache()
     if args.workload.startswith("rmat"):
         n2, s2, d2, _ = make_workload("grid4096", dev, seed)
         g2 = cc.cc_init(n2, s2, d2, stream=stream.cuda_stream)

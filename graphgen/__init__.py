@@ -41,8 +41,7 @@ import torch
 __all__ = [
     "BASE_SEED", "mix64_int", "stream_key", "uniform64", "uniform_below",
     "path", "grid", "rmat", "er", "caterpillar", "components64", "delaunay_like",
-    "batch_mix_params", "batch_graph", "batch_mix", "permute_and_shuffle",
-]
+    "batch_mix_params", "batch_graph", "batch_mix", "permute_and_shuffle", "to_csr"]
 
 BASE_SEED = 2311028110
 SHUFFLE_BLOCK = 1 << 30
@@ -440,3 +439,26 @@ def _edge_count(p: dict) -> int:
         keep = _hi32(uniform64(stream_key(p["seed"], 1), 0, tot, "cpu")) >= _threshold(Fraction(5, 100))
         return int(keep.sum())
     return p["m"]
+
+
+def to_csr(n: int, src: torch.Tensor, dst: torch.Tensor, symmetric: bool = False):
+    """CSR form of an edge list: ``(offsets int64[n + 1], cols)``.
+
+    Entry order: rows ascending; within a row the entries keep the order of
+    the edge list (stable sort).  ``symmetric=False``: edge e is the entry
+    (src[e], dst[e]).  ``symmetric=True``: edge e is stored in both rows,
+    (src[e], dst[e]) and (dst[e], src[e]) (a self-loop twice in its row), so
+    nnz = 2 * m.  Runs on the tensors' device; no arithmetic of the method.
+    """
+    if symmetric:
+        rows = torch.cat([src, dst])
+        cols = torch.cat([dst, src])
+    else:
+        rows, cols = src, dst
+    order = torch.sort(rows.to(torch.int64), stable=True).indices
+    cols = cols[order].contiguous()
+    counts = torch.bincount(rows.to(torch.int64), minlength=n)
+    off = torch.zeros(n + 1, dtype=torch.int64, device=src.device)
+    if n:
+        off[1:] = torch.cumsum(counts, 0)
+    return off, cols

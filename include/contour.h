@@ -48,7 +48,7 @@ typedef enum {
 } cc_status;
 
 enum { CC_ID32 = 32, CC_ID64 = 64 };
-enum { CC_COO = 0, CC_CSR = 1 };
+enum { CC_COO = 0, CC_CSR = 1, CC_CSR_NATIVE = 2, CC_CSR_NATIVE_SYM = 3 };
 enum { CC_SYNC = 0, CC_ASYNC = 1 };
 /* Operator order: h >= 1 is MM^h of Def. 3; CC_ORDER_FULL follows each label
  * chain to its root (at most 1024 hops, the "C-m" variant with m = 1024 of
@@ -81,14 +81,31 @@ typedef struct {
  *                     <src[e], dst[e]> (self-loops and repeats allowed), or
  *   layout == CC_CSR: a = int64_t offsets[n+1], b = cols[nnz], nnz = m_or_nnz;
  *                     every stored entry (r, cols[k]) becomes one edge.  A
- *                     symmetric CSR therefore yields every edge twice.
+ *                     symmetric CSR therefore yields every edge twice.  The
+ *                     rows are expanded on the device into an edge list.
+ *   layout == CC_CSR_NATIVE: the same input, kept as CSR: each sweep walks the
+ *                     rows directly (no per-entry row array is built; the
+ *                     handle adds one int32 row index per 4 entries).  Every
+ *                     entry (r, cols[k]) is one edge <r, cols[k]>.
+ *   layout == CC_CSR_NATIVE_SYM: a symmetric CSR (each undirected edge stored
+ *                     in both rows) kept as CSR; a sweep applies the operator
+ *                     only to the entries with cols[k] < r, i.e. once per
+ *                     undirected edge.  Self-loops are dropped (they never
+ *                     change a label).  The input is not checked for
+ *                     symmetry: an edge stored only as (r, c) with c > r is
+ *                     never applied.
+ *   The native CSR layouts take int32 ids only (CC_EINVAL otherwise), do not
+ *   support cc_graph_reorder (CC_EINVAL), and count m = nnz stored entries
+ *   in cc_graph_info and cc_stats.edges_per_s.
  * Ids have the type chosen by id_bits.
  *
  * on_device == 0: a and b are host arrays; they are copied to the device and
  *                 may be freed after the call returns.
  * on_device == 1: a and b are device arrays.  A COO pair whose pointers are
  *                 16-byte aligned is borrowed (no copy) and must stay alive
- *                 and unchanged until cc_free; otherwise it is copied.
+ *                 and unchanged until cc_free; otherwise it is copied.  For
+ *                 the native CSR layouts the offsets (8-byte aligned) and the
+ *                 columns (16-byte aligned) are borrowed under the same rule.
  *
  * Every id is checked on the device: CC_EIDRANGE if any endpoint lies
  * outside [0, n) (CSR: also CC_EINVAL for offsets that are not a
@@ -316,9 +333,32 @@ cc_status cc_sched_train_step(const float *features_norm, const int32_t *labels,
  *   CC_REORDER_SRC     sort the (src, dst) pairs by src
  *   CC_REORDER_LOWDEG  orient each edge from its lower-degree endpoint (ties:
  *                      smaller id) and sort by that endpoint
+ *   CC_REORDER_HUB     CC_REORDER_LOWDEG, then the vertices of highest degree
+ *                      (at most 24,576, each of degree >= 16) become hubs
+ *                      whose labels every sweep reads from a shared-memory
+ *                      table: in the stored dst array, an entry d < 0 stands
+ *                      for vertex hubs[~d] (cc_graph_hubs).  A graph without
+ *                      such vertices keeps plain ids.  A hub-encoded handle
+ *                      cannot be reordered again (CC_EINVAL).
+ * CC_EINVAL for native CSR handles.
  */
-enum { CC_REORDER_SRC = 1, CC_REORDER_LOWDEG = 2 };
+enum { CC_REORDER_SRC = 1, CC_REORDER_LOWDEG = 2, CC_REORDER_HUB = 3 };
 cc_status cc_graph_reorder(cc_graph *g, int method);
+
+/* The hub table of a CC_REORDER_HUB handle: *hubs (device, *k int32 ids) is
+ * NULL and *k is 0 when the edges carry no hub entries.  Valid until cc_free
+ * or the next cc_graph_reorder. */
+cc_status cc_graph_hubs(const cc_graph *g, const int32_t **hubs, int32_t *k);
+
+/* How cc_run drives the sweep loop.  CC_LAUNCH_GRAPH (default): one CUDA
+ * graph whose conditional WHILE node repeats the check blocks on the device,
+ * with no host round trip.  CC_LAUNCH_HOST: the host enqueues one check block
+ * at a time and reads the convergence flag after each; slower (a stream
+ * synchronisation per block), but every kernel is an ordinary launch, for
+ * profilers and debuggers that do not follow conditional graph nodes.  Both
+ * give identical labels and sweep counts. */
+enum { CC_LAUNCH_GRAPH = 0, CC_LAUNCH_HOST = 1 };
+cc_status cc_graph_set_launch(cc_graph *g, int launch);
 
 /* Make later cc_run calls on g enqueue on another stream (default: the stream
  * passed to cc_init). */
@@ -329,7 +369,9 @@ cc_status cc_graph_info(const cc_graph *g, int64_t *n, int64_t *m);
 
 /* Device pointers of the handle's edge arrays (the borrowed input, or the
  * handle's own copy after cc_init copied or cc_graph_reorder reordered it);
- * valid until cc_free or the next cc_graph_reorder. */
+ * valid until cc_free or the next cc_graph_reorder.  For the native CSR
+ * layouts *src receives the int64 offsets and *dst the columns; after
+ * CC_REORDER_HUB the dst array holds hub entries ~s (see cc_graph_hubs). */
 cc_status cc_graph_edges(const cc_graph *g, const void **src, const void **dst);
 
 /* Release a handle and every device buffer it owns.  NULL is ignored.  The

@@ -16,13 +16,14 @@ import os
 
 __all__ = [
     "CC_OK", "CC_EINVAL", "CC_EIDRANGE", "CC_ENOMEM", "CC_ECUDA", "CC_ENOTCONVERGED",
-    "CC_ETIMEOUT", "CC_ID32", "CC_ID64", "CC_COO", "CC_CSR", "CC_SYNC", "CC_ASYNC",
+    "CC_ETIMEOUT", "CC_ID32", "CC_ID64", "CC_COO", "CC_CSR", "CC_CSR_NATIVE", "CC_CSR_NATIVE_SYM",
+    "CC_SYNC", "CC_ASYNC",
     "CC_ORDER_FULL", "CC_ORDER_AUTO", "CC_ORDER_11MM", "CC_ORDER_1M1M", "CC_NOALLOC_MAX_N", "CCError", "cc_stats", "cc_graph", "lib", "LIB_PATH",
     "cc_init", "cc_run", "cc_run_noalloc", "cc_free", "cc_release_memory", "cc_batch_plan", "cc_batch_init",
     "cc_batch_run", "cc_batch_set_schedule", "cc_batch_run_scheduled", "cc_batch_tuning",
     "cc_batch_set_tuning", "cc_batch_reorder", "cc_batch_edges", "cc_batch_free", "cc_batch", "cc_sched_load", "cc_sched_blob_bytes",
     "cc_sched_param_count", "cc_sched_decode", "cc_graph_features", "cc_batch_features",
-    "cc_sched_predict", "cc_sched_train", "load_default_scheduler", "SCHED_WEIGHTS_PATH", "cc_sched_train_step", "CC_SCHED_FEATURES", "CC_SCHED_CLASSES", "cc_graph_info", "cc_graph_edges", "cc_graph_set_stream", "cc_graph_reorder", "CC_REORDER_SRC", "CC_REORDER_LOWDEG", "cc_strerror",
+    "cc_sched_predict", "cc_sched_train", "load_default_scheduler", "SCHED_WEIGHTS_PATH", "cc_sched_train_step", "CC_SCHED_FEATURES", "CC_SCHED_CLASSES", "cc_graph_info", "cc_graph_edges", "cc_graph_set_stream", "cc_graph_reorder", "CC_REORDER_SRC", "CC_REORDER_LOWDEG", "CC_REORDER_HUB", "cc_graph_hubs", "cc_graph_set_launch", "CC_LAUNCH_GRAPH", "CC_LAUNCH_HOST", "cc_strerror",
     "cc_last_error",
 ]
 
@@ -30,7 +31,7 @@ LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libcontour.
 
 CC_OK, CC_EINVAL, CC_EIDRANGE, CC_ENOMEM, CC_ECUDA, CC_ENOTCONVERGED, CC_ETIMEOUT = range(7)
 CC_ID32, CC_ID64 = 32, 64
-CC_COO, CC_CSR = 0, 1
+CC_COO, CC_CSR, CC_CSR_NATIVE, CC_CSR_NATIVE_SYM = 0, 1, 2, 3
 CC_SYNC, CC_ASYNC = 0, 1
 CC_ORDER_FULL, CC_ORDER_AUTO = 0, -1
 CC_ORDER_11MM, CC_ORDER_1M1M = -2, -3
@@ -438,7 +439,7 @@ def cc_sched_train_step(features_std, labels, params, lr):
     return p, loss.value
 
 
-CC_REORDER_SRC, CC_REORDER_LOWDEG = 1, 2
+CC_REORDER_SRC, CC_REORDER_LOWDEG, CC_REORDER_HUB = 1, 2, 3
 lib.cc_graph_reorder.argtypes = [_p, _int]
 lib.cc_graph_reorder.restype = _int
 
@@ -459,6 +460,27 @@ def cc_graph_edges(g):
     a, b = _p(), _p()
     _check(lib.cc_graph_edges(g, ctypes.byref(a), ctypes.byref(b)), "cc_graph_edges")
     return a.value, b.value
+
+
+lib.cc_graph_hubs.argtypes = [_p, ctypes.POINTER(_p), ctypes.POINTER(_i32)]
+lib.cc_graph_hubs.restype = _int
+
+
+def cc_graph_hubs(g):
+    """(device pointer, count) of the hub table of a CC_REORDER_HUB handle."""
+    a, k = _p(), _i32(0)
+    _check(lib.cc_graph_hubs(g, ctypes.byref(a), ctypes.byref(k)), "cc_graph_hubs")
+    return a.value, k.value
+
+
+CC_LAUNCH_GRAPH, CC_LAUNCH_HOST = 0, 1
+lib.cc_graph_set_launch.argtypes = [_p, _int]
+lib.cc_graph_set_launch.restype = _int
+
+
+def cc_graph_set_launch(g, launch):
+    """CC_LAUNCH_GRAPH (device-side loop) or CC_LAUNCH_HOST (host-polled blocks)."""
+    _check(lib.cc_graph_set_launch(g, int(launch)), "cc_graph_set_launch")
 
 
 def cc_graph_info(g):

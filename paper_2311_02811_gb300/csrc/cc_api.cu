@@ -22,6 +22,8 @@
 #include "../../include/contour.h"
 #include "cc_internal.h"
 #include "mm_kernels.cuh"
+#include "csr_kernels.cuh"
+#include "hub_kernels.cuh"
 
 using cc::Ctl;
 
@@ -170,9 +172,16 @@ struct LoopGraph {
 struct cc_graph {
     int64_t n = 0, m = 0;
     int id_bits = 32;
-    void* src = nullptr;
-    void* dst = nullptr;
+    int layout = CC_COO;  // CC_COO (also after CSR expansion), CC_CSR_NATIVE or CC_CSR_NATIVE_SYM
+    void* src = nullptr;  // COO only
+    void* dst = nullptr;  // COO: dst ids; native CSR: columns
     bool own_edges = false;
+    int64_t* off = nullptr;   // native CSR: row offsets (n + 1)
+    bool own_off = false;
+    int32_t* seg = nullptr;   // native CSR: row of every 4th entry
+    int32_t* hubs = nullptr;  // CC_REORDER_HUB: dst entry ~s names hubs[s]
+    int hub_k = 0;
+    int launch = CC_LAUNCH_GRAPH;  // or CC_LAUNCH_HOST (cc_graph_set_launch)
     void* L = nullptr;   // working labels when the caller's output is on the host
     void* Lu = nullptr;  // update array of synchronous runs
     Ctl* ctl = nullptr;
@@ -202,6 +211,9 @@ static void destroy(cc_graph* g) {
         cc::dfree(g->src, g->stream);
         cc::dfree(g->dst, g->stream);
     }
+    if (g->own_off) cc::dfree(g->off, g->stream);
+    cc::dfree(g->seg, g->stream);
+    cc::dfree(g->hubs, g->stream);
     cc::dfree(g->L, g->stream);
     cc::dfree(g->Lu, g->stream);
     cc::dfree(g->ctl, g->stream);
@@ -231,6 +243,32 @@ static int grid_for(K kernel, int64_t work_items) {
 template <int H, bool SYNC, typename IdT>
 static cudaError_t launch_sweep_t(const cc_graph* g, IdT* L, IdT* Lu, int h, int32_t* flag,
                                   int first, cudaStream_t s, int gate = 0) {
+    if constexpr (sizeof(IdT) == 4) {
+        if (g->layout == CC_CSR_NATIVE || g->layout == CC_CSR_NATIVE_SYM) {
+            auto kc = cc::csr_sweep_kernel<H, SYNC>;
+            const int grid = grid_for(kc, (g->m + cc::kCsrGroup - 1) / cc::kCsrGroup + 1);
+            kc<<<grid, kThreads, 0, s>>>(g->off, static_cast<const int32_t*>(g->dst), g->seg, g->m, L, Lu, h,
+                                          flag, g->ctl, first, gate, g->layout == CC_CSR_NATIVE_SYM);
+            return cudaGetLastError();
+        }
+    }
+    if constexpr (sizeof(IdT) == 4) {
+        if (g->hub_k > 0) {
+            auto kh = cc::mm_sweep_hub_kernel<H, SYNC>;
+            const size_t smem = (size_t)g->hub_k * 2 * sizeof(int32_t);
+            static bool attr = false;
+            if (!attr) {
+                cudaError_t e = cudaFuncSetAttribute(kh, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                     cc::kHubMax * 2 * (int)sizeof(int32_t));
+                if (e != cudaSuccess) return e;
+                attr = true;
+            }
+            kh<<<cc::device_sms(), cc::kHubThreads, smem, s>>>(
+                static_cast<const int32_t*>(g->src), static_cast<const int32_t*>(g->dst), g->m, L, Lu, h, flag,
+                g->ctl, first, gate, g->hubs, g->hub_k);
+            return cudaGetLastError();
+        }
+    }
     constexpr int G = (H == 1) ? 2 : 1;  // edge groups of 4 per thread per step
     auto k = cc::mm_sweep_kernel<H, SYNC, G, IdT>;
     const int grid = grid_for(k, g->m / (4 * G) + 1);
@@ -262,9 +300,24 @@ static cudaError_t launch_copy(IdT* dst, const IdT* src, int64_t n, cudaStream_t
 // One check block: c sweeps (the flag only from the last), then the check.
 // A per-iteration order schedule (C-11mm, C-1m1m) has one sweep per block,
 // run by whichever of its two gated kernels the control word selects.
+// The end of a check block for host-polled runs: the bookkeeping of
+// check_kernel without the graph's loop condition; the host reads ctl.
+static __global__ void check_host_kernel(Ctl* ctl, int32_t block_sweeps, int sched) {
+    if (threadIdx.x == 0) {
+        const int32_t f = ctl->flag;
+        ctl->flag = 0;
+        ctl->sweeps += block_sweeps;
+        if (sched == 1) ctl->sched_h = ctl->sweeps < 2 ? 1 : cc::kFullChainHops;
+        if (sched == 2) ctl->sched_h = (ctl->sweeps % 2 == 0) ? 1 : cc::kFullChainHops;
+        ctl->converged = (f == 0);
+    }
+}
+
+// host_polled: end the block with check_host_kernel instead of the graph's
+// loop-condition update.
 template <typename IdT>
 static cudaError_t enqueue_block(cc_graph* g, int order, int mode, int c, IdT* L, IdT* Lu,
-                                 cudaGraphConditionalHandle loop, cudaStream_t s) {
+                                 cudaGraphConditionalHandle loop, cudaStream_t s, bool host_polled = false) {
     if (order == CC_ORDER_11MM || order == CC_ORDER_1M1M) {
         const int first = mode == CC_SYNC ? 1 : 0;
         int32_t* flag = &g->ctl->flag;
@@ -280,7 +333,8 @@ static cudaError_t enqueue_block(cc_graph* g, int order, int mode, int c, IdT* L
             e = launch_copy<IdT>(L, Lu, g->n, s);
             if (e != cudaSuccess) return e;
         }
-        cc::check_kernel<<<1, 32, 0, s>>>(g->ctl, 1, loop, order == CC_ORDER_11MM ? 1 : 2);
+        if (host_polled) check_host_kernel<<<1, 32, 0, s>>>(g->ctl, 1, order == CC_ORDER_11MM ? 1 : 2);
+        else cc::check_kernel<<<1, 32, 0, s>>>(g->ctl, 1, loop, order == CC_ORDER_11MM ? 1 : 2);
         return cudaGetLastError();
     }
     for (int j = 0; j < c; ++j) {
@@ -297,7 +351,8 @@ static cudaError_t enqueue_block(cc_graph* g, int order, int mode, int c, IdT* L
             if (e != cudaSuccess) return e;
         }
     }
-    cc::check_kernel<<<1, 32, 0, s>>>(g->ctl, c, loop);
+    if (host_polled) check_host_kernel<<<1, 32, 0, s>>>(g->ctl, c, 0);
+    else cc::check_kernel<<<1, 32, 0, s>>>(g->ctl, c, loop);
     return cudaGetLastError();
 }
 
@@ -371,6 +426,57 @@ static cc_status get_loop(cc_graph* g, int order, int mode, int c, void* L, void
 // ---------------------------------------------------------------------------
 // cc_init
 // ---------------------------------------------------------------------------
+
+// Native CSR (int32 ids): keep offsets and columns, validate both, and index
+// the row of every 4th entry.
+static cc_status init_csr_native(cc_graph* g, int layout, const void* a, const void* b, int64_t cnt,
+                                 int on_device, cudaStream_t s) {
+    const int64_t n = g->n;
+    g->layout = layout;
+    g->m = cnt;
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    if (on_device && (reinterpret_cast<uintptr_t>(a) & 7) == 0) {
+        g->off = static_cast<int64_t*>(const_cast<void*>(a));
+    } else {
+        CC_CUDA(cc::dmalloc(reinterpret_cast<void**>(&g->off), (size_t)(n + 1) * sizeof(int64_t), s));
+        g->own_off = true;
+        CC_CUDA(cudaMemcpyAsync(g->off, a, (size_t)(n + 1) * sizeof(int64_t), kind, s));
+    }
+    if (cnt > 0) {
+        if (on_device && (reinterpret_cast<uintptr_t>(b) & 15) == 0) {
+            g->dst = const_cast<void*>(b);
+        } else {
+            CC_CUDA(cc::dmalloc(&g->dst, (size_t)cnt * sizeof(int32_t), s));
+            g->own_edges = true;
+            CC_CUDA(cudaMemcpyAsync(g->dst, b, (size_t)cnt * sizeof(int32_t), kind, s));
+        }
+    }
+    auto kv = cc::validate_offsets_kernel;
+    kv<<<grid_for(kv, n + 1), kThreads, 0, s>>>(g->off, n, cnt, g->ctl);
+    CC_LAUNCHED();
+    CC_CUDA(cudaMemcpyAsync(g->ctl_h, g->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
+    CC_CUDA(cudaStreamSynchronize(s));
+    if (g->ctl_h->bad_count)
+        return set_error(CC_EINVAL, "CSR offsets are not non-decreasing from 0 to nnz=%lld (first bad index %llu)",
+                         (long long)cnt, g->ctl_h->first_bad);
+    if (cnt > 0) {
+        const int32_t* cols = static_cast<const int32_t*>(g->dst);
+        auto ki = cc::validate_ids_kernel<int32_t>;
+        ki<<<grid_for(ki, cnt / 4 + 1), kThreads, 0, s>>>(cols, cols, cnt, n, g->ctl);
+        CC_LAUNCHED();
+        const int64_t groups = (cnt + cc::kCsrGroup - 1) / cc::kCsrGroup;
+        CC_CUDA(cc::dmalloc(reinterpret_cast<void**>(&g->seg), (size_t)groups * sizeof(int32_t), s));
+        auto ks = cc::csr_seg_rows_kernel;
+        ks<<<grid_for(ks, groups), kThreads, 0, s>>>(g->off, n, cnt, g->seg);
+        CC_LAUNCHED();
+    }
+    CC_CUDA(cudaMemcpyAsync(g->ctl_h, g->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
+    CC_CUDA(cudaStreamSynchronize(s));
+    if (g->ctl_h->bad_count)
+        return set_error(CC_EIDRANGE, "%llu column ids outside [0, %lld) (first at entry %llu)",
+                         g->ctl_h->bad_count / 2, (long long)n, g->ctl_h->first_bad);
+    return CC_OK;
+}
 
 template <typename IdT>
 static cc_status init_edges(cc_graph* g, int layout, const void* a, const void* b, int64_t cnt,
@@ -448,8 +554,11 @@ extern "C" cc_status cc_init(cc_graph** out, int64_t n, int id_bits, int layout,
     if (n < 0 || cnt < 0) return set_error(CC_EINVAL, "cc_init: negative n or m");
     if (id_bits != CC_ID32 && id_bits != CC_ID64) return set_error(CC_EINVAL, "cc_init: id_bits must be 32 or 64");
     if (id_bits == CC_ID32 && n > 0x7fffffffLL) return set_error(CC_EINVAL, "cc_init: n >= 2^31 needs CC_ID64");
-    if (layout != CC_COO && layout != CC_CSR) return set_error(CC_EINVAL, "cc_init: bad layout");
-    if (layout == CC_CSR && !a) return set_error(CC_EINVAL, "cc_init: CSR offsets are NULL");
+    if (layout != CC_COO && layout != CC_CSR && layout != CC_CSR_NATIVE && layout != CC_CSR_NATIVE_SYM)
+        return set_error(CC_EINVAL, "cc_init: bad layout");
+    const bool native = layout == CC_CSR_NATIVE || layout == CC_CSR_NATIVE_SYM;
+    if (layout != CC_COO && !a) return set_error(CC_EINVAL, "cc_init: CSR offsets are NULL");
+    if (native && id_bits != CC_ID32) return set_error(CC_EINVAL, "cc_init: the native CSR layouts take int32 ids");
     if (cnt > 0 && (!a || !b)) return set_error(CC_EINVAL, "cc_init: edge arrays are NULL");
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
 
@@ -475,8 +584,9 @@ extern "C" cc_status cc_init(cc_graph** out, int64_t n, int id_bits, int layout,
     }
     cc::ctl_reset_kernel<<<1, 32, 0, s>>>(g->ctl, 1, 0);
     if (cudaGetLastError() != cudaSuccess) return fail(set_error(CC_ECUDA, "cc_init: launch failed"));
-    st = (id_bits == 64) ? init_edges<int64_t>(g, layout, a, b, cnt, on_device, s)
-                         : init_edges<int32_t>(g, layout, a, b, cnt, on_device, s);
+    st = native ? init_csr_native(g, layout, a, b, cnt, on_device, s)
+         : (id_bits == 64) ? init_edges<int64_t>(g, layout, a, b, cnt, on_device, s)
+                           : init_edges<int32_t>(g, layout, a, b, cnt, on_device, s);
     if (st != CC_OK) return fail(st);
     *out = g;
     return CC_OK;
@@ -567,7 +677,8 @@ static cc_status run_impl(cc_graph* g, int order, int mode, int c, int32_t max_s
         Lu = g->Lu;
     }
     cudaGraphExec_t loop = nullptr;
-    {
+    const bool host_polled = g->launch == CC_LAUNCH_HOST;
+    if (!host_polled) {
         cc_status st = get_loop(g, order, mode, c, L, Lu, &loop);
         if (st != CC_OK) return st;
     }
@@ -586,7 +697,19 @@ static cc_status run_impl(cc_graph* g, int order, int mode, int c, int32_t max_s
                              g->ctl_h->bad_count, g->ctl_h->first_bad);
     }
     CC_CUDA(cudaEventRecord(g->evl0, s));
-    CC_CUDA(cudaGraphLaunch(loop, s));
+    if (host_polled) {
+        // one check block at a time; the host reads the control block after each
+        while (true) {
+            CC_CUDA(g->id_bits == 64
+                        ? enqueue_block<int64_t>(g, order, mode, c, (int64_t*)L, (int64_t*)Lu, 0, s, true)
+                        : enqueue_block<int32_t>(g, order, mode, c, (int32_t*)L, (int32_t*)Lu, 0, s, true));
+            CC_CUDA(cudaMemcpyAsync(g->ctl_h, g->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
+            CC_CUDA(cudaStreamSynchronize(s));
+            if (g->ctl_h->converged || g->ctl_h->sweeps >= max_sweeps) break;
+        }
+    } else {
+        CC_CUDA(cudaGraphLaunch(loop, s));
+    }
     CC_CUDA(cudaEventRecord(g->evl1, s));
     CC_CUDA(g->id_bits == 64 ? enqueue_compress<int64_t>(g, (int64_t*)L, s)
                              : enqueue_compress<int32_t>(g, (int32_t*)L, s));
@@ -605,7 +728,11 @@ static cc_status run_impl(cc_graph* g, int order, int mode, int c, int32_t max_s
         stats->solve_ms = ms;
         stats->loop_ms = lms;
         stats->edges_per_s = ms > 0 ? (double)g->m / (ms * 1e-3) : 0.0;
-        double per = 2.0 * B * (double)g->m + B * (double)g->n;
+        // COO: both id arrays and every label once; native CSR: columns,
+        // offsets and every label once
+        double per = (g->layout == CC_CSR_NATIVE || g->layout == CC_CSR_NATIVE_SYM)
+                         ? B * (double)g->m + 8.0 * (double)(g->n + 1) + B * (double)g->n
+                         : 2.0 * B * (double)g->m + B * (double)g->n;
         if (mode == CC_SYNC) per += 3.0 * B * (double)g->n;
         stats->alg_bytes = per * h.sweeps;
     }
@@ -619,8 +746,28 @@ static cc_status run_impl(cc_graph* g, int order, int mode, int c, int32_t max_s
 
 extern "C" cc_status cc_graph_edges(const cc_graph* g, const void** src, const void** dst) {
     if (!g) return set_error(CC_EINVAL, "cc_graph_edges: g is NULL");
+    if (g->layout == CC_CSR_NATIVE || g->layout == CC_CSR_NATIVE_SYM) {
+        if (src) *src = g->off;
+        if (dst) *dst = g->dst;
+        return CC_OK;
+    }
     if (src) *src = g->src;
     if (dst) *dst = g->dst;
+    return CC_OK;
+}
+
+extern "C" cc_status cc_graph_set_launch(cc_graph* g, int launch) {
+    if (!g) return set_error(CC_EINVAL, "cc_graph_set_launch: g is NULL");
+    if (launch != CC_LAUNCH_GRAPH && launch != CC_LAUNCH_HOST)
+        return set_error(CC_EINVAL, "cc_graph_set_launch: launch must be CC_LAUNCH_GRAPH or CC_LAUNCH_HOST");
+    g->launch = launch;
+    return CC_OK;
+}
+
+extern "C" cc_status cc_graph_hubs(const cc_graph* g, const int32_t** hubs, int32_t* k) {
+    if (!g) return set_error(CC_EINVAL, "cc_graph_hubs: g is NULL");
+    if (hubs) *hubs = g->hubs;
+    if (k) *k = g->hub_k;
     return CC_OK;
 }
 
@@ -653,6 +800,16 @@ namespace cc {
 const void* graph_src(const cc_graph* g) { return g->src; }
 const void* graph_dst(const cc_graph* g) { return g->dst; }
 int graph_id_bits(const cc_graph* g) { return g->id_bits; }
+int graph_layout(const cc_graph* g) { return g->layout; }
+int graph_hub_count(const cc_graph* g) { return g->hub_k; }
+const int32_t* graph_hubs(const cc_graph* g) { return g->hubs; }
+void graph_set_hubs(cc_graph* g, int32_t* hubs, int k) {
+    free_loops(g);  // loop graphs captured the plain sweep kernel
+    dfree(g->hubs, g->stream);
+    g->hubs = hubs;
+    g->hub_k = k;
+}
+const int64_t* graph_csr_off(const cc_graph* g) { return g->off; }
 cudaStream_t graph_stream(const cc_graph* g) { return g->stream; }
 SchedCtx** graph_sched_slot(cc_graph* g) { return &g->sched; }
 cc_status graph_replace_edges(cc_graph* g, void* src, void* dst) {
@@ -660,6 +817,9 @@ cc_status graph_replace_edges(cc_graph* g, void* src, void* dst) {
     free_loops(g);
     sched_ctx_free(g->sched);
     g->sched = nullptr;
+    dfree(g->hubs, g->stream);
+    g->hubs = nullptr;
+    g->hub_k = 0;
     if (g->own_edges) {
         dfree(g->src, g->stream);
         dfree(g->dst, g->stream);

@@ -31,6 +31,12 @@ int persistent_blocks(const void* fn, int threads, size_t smem);
 const void* graph_src(const cc_graph* g);
 const void* graph_dst(const cc_graph* g);
 int graph_id_bits(const cc_graph* g);
+int graph_layout(const cc_graph* g);            // CC_COO or a native CSR layout
+const int64_t* graph_csr_off(const cc_graph* g);  // native CSR row offsets
+int graph_hub_count(const cc_graph* g);           // hubs of a CC_REORDER_HUB edge list (0: none)
+const int32_t* graph_hubs(const cc_graph* g);
+// Hand the hub table (device array of k ids) to the handle, which frees it.
+void graph_set_hubs(cc_graph* g, int32_t* hubs, int k);
 cc_status graph_nm(const cc_graph* g, long long* n, long long* m);
 cudaStream_t graph_stream(const cc_graph* g);
 SchedCtx** graph_sched_slot(cc_graph* g);

@@ -13,11 +13,20 @@
 //                      smaller id) to the other and sort by that endpoint, so
 //                      the high-degree side -- whose labels stay hot in cache --
 //                      is the scattered one
+//   CC_REORDER_HUB     CC_REORDER_LOWDEG, then the (at most kHubMax) vertices
+//                      of highest degree, if their degree is at least
+//                      kHubMinDegree, become hubs: a dst entry naming hub
+//                      number s is stored as ~s, and the sweep reads the hubs'
+//                      labels from a shared-memory table (hub_kernels.cuh)
 #include <cub/device/device_radix_sort.cuh>
 #include <cuda_runtime.h>
 
+#include <algorithm>
+#include <vector>
+
 #include "../../include/contour.h"
 #include "cc_internal.h"
+#include "hub_kernels.cuh"
 
 namespace {
 
@@ -42,13 +51,34 @@ __global__ void orient_kernel(const int32_t* src, const int32_t* dst, int64_t m,
     }
 }
 
-__global__ void range_check_kernel(const uint32_t* a, const uint32_t* b, int64_t m, int64_t n,
+// a[e] must be an id in [0, n); b[e] an id, or ~s for a hub slot s < K
+__global__ void range_check_kernel(const uint32_t* a, const uint32_t* b, int64_t m, int64_t n, int64_t K,
                                    unsigned long long* bad) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     unsigned long long cnt = 0;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += stride)
-        cnt += ((int64_t)a[e] >= n) + ((int64_t)b[e] >= n);
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += stride) {
+        const int32_t bv = (int32_t)b[e];
+        cnt += ((int64_t)a[e] >= n) + (bv >= 0 ? (int64_t)bv >= n : (int64_t)(~bv) >= K);
+    }
     if (cnt) atomicAdd(bad, cnt);
+}
+
+__global__ void iota_u32_kernel(uint32_t* x, int64_t n) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) x[i] = (uint32_t)i;
+}
+
+__global__ void hub_slots_kernel(const uint32_t* hubs, int K, int32_t* slot_of) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < K; i += gridDim.x * blockDim.x)
+        slot_of[hubs[i]] = i;
+}
+
+__global__ void hub_encode_kernel(uint32_t* v, int64_t m, const int32_t* slot_of) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += stride) {
+        const int32_t s = slot_of[v[e]];
+        if (s >= 0) v[e] = (uint32_t)(~s);
+    }
 }
 
 int bits_for(int64_t n) {
@@ -66,14 +96,75 @@ int bits_for(int64_t n) {
         }                                                                            \
     } while (0)
 
+// The hubs: vertices sorted by degree (descending), the first ones of degree
+// >= kHubMinDegree, at most kHubMax.  v (m high-side ids) is rewritten in
+// place: an id that is hub number s becomes ~s.  *hubs_out (owned by the
+// caller) receives the K hub ids; K = 0 leaves v unchanged.
+cc_status select_and_encode_hubs(const int32_t* deg, int64_t n, uint32_t* v, int64_t m, cudaStream_t s,
+                                 uint32_t** hubs_out, int* k_out) {
+    *hubs_out = nullptr;
+    *k_out = 0;
+    cc_status st = CC_OK;
+    uint32_t *ids = nullptr, *ids_sorted = nullptr;
+    int32_t *deg_sorted = nullptr, *slot_of = nullptr;
+    void* tmp = nullptr;
+    size_t tmp_bytes = 0;
+    const int grid = cc::device_sms() * 8;
+    const int cap = (int)std::min<int64_t>(n, cc::kHubMax);
+    std::vector<int32_t> top(cap > 0 ? cap : 1);
+    int K = 0;
+    RCUDA(cc::dmalloc(reinterpret_cast<void**>(&ids), (size_t)n * sizeof(uint32_t), s));
+    RCUDA(cc::dmalloc(reinterpret_cast<void**>(&ids_sorted), (size_t)n * sizeof(uint32_t), s));
+    RCUDA(cc::dmalloc(reinterpret_cast<void**>(&deg_sorted), (size_t)n * sizeof(int32_t), s));
+    iota_u32_kernel<<<grid, 256, 0, s>>>(ids, n);
+    RCUDA(cudaGetLastError());
+    RCUDA(cub::DeviceRadixSort::SortPairsDescending(nullptr, tmp_bytes, deg, deg_sorted, ids, ids_sorted,
+                                                    (long long)n, 0, 32, s));
+    RCUDA(cc::dmalloc(&tmp, tmp_bytes, s));
+    RCUDA(cub::DeviceRadixSort::SortPairsDescending(tmp, tmp_bytes, deg, deg_sorted, ids, ids_sorted,
+                                                    (long long)n, 0, 32, s));
+    if (cap > 0) RCUDA(cudaMemcpyAsync(top.data(), deg_sorted, (size_t)cap * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    RCUDA(cudaStreamSynchronize(s));
+    while (K < cap && top[K] >= cc::kHubMinDegree) ++K;
+    if (K > 0) {
+        RCUDA(cc::dmalloc(reinterpret_cast<void**>(&slot_of), (size_t)n * sizeof(int32_t), s));
+        RCUDA(cudaMemsetAsync(slot_of, 0xff, (size_t)n * sizeof(int32_t), s));  // -1: not a hub
+        hub_slots_kernel<<<(K + 255) / 256, 256, 0, s>>>(ids_sorted, K, slot_of);
+        RCUDA(cudaGetLastError());
+        hub_encode_kernel<<<grid, 256, 0, s>>>(v, m, slot_of);
+        RCUDA(cudaGetLastError());
+        RCUDA(cc::dmalloc(reinterpret_cast<void**>(hubs_out), (size_t)K * sizeof(uint32_t), s));
+        RCUDA(cudaMemcpyAsync(*hubs_out, ids_sorted, (size_t)K * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
+        RCUDA(cudaStreamSynchronize(s));
+        *k_out = K;
+    }
+done:
+    cc::dfree(ids, s);
+    cc::dfree(ids_sorted, s);
+    cc::dfree(deg_sorted, s);
+    cc::dfree(slot_of, s);
+    cc::dfree(tmp, s);
+    if (st != CC_OK && *hubs_out) {
+        cc::dfree(*hubs_out, s);
+        *hubs_out = nullptr;
+        *k_out = 0;
+    }
+    return st;
+}
+
 }  // namespace
 
 extern "C" cc_status cc_graph_reorder(cc_graph* g, int method) {
     cc::NvtxRange range("cc_graph_reorder");
     if (!g) return cc::set_error(CC_EINVAL, "cc_graph_reorder: g is NULL");
-    if (method != CC_REORDER_SRC && method != CC_REORDER_LOWDEG)
-        return cc::set_error(CC_EINVAL, "cc_graph_reorder: method must be CC_REORDER_SRC or CC_REORDER_LOWDEG");
+    if (method != CC_REORDER_SRC && method != CC_REORDER_LOWDEG && method != CC_REORDER_HUB)
+        return cc::set_error(CC_EINVAL,
+                             "cc_graph_reorder: method must be CC_REORDER_SRC, CC_REORDER_LOWDEG or CC_REORDER_HUB");
     if (cc::graph_id_bits(g) != 32) return cc::set_error(CC_EINVAL, "cc_graph_reorder: int32 ids only");
+    if (cc::graph_layout(g) != CC_COO)
+        return cc::set_error(CC_EINVAL, "cc_graph_reorder: a native CSR handle keeps the caller's row order");
+    if (cc::graph_hub_count(g) > 0)
+        return cc::set_error(CC_EINVAL, "cc_graph_reorder: the edges are already hub-encoded (CC_REORDER_HUB)");
     long long n = 0, m = 0;
     cc::graph_nm(g, &n, &m);
     if (m == 0) return CC_OK;
@@ -85,10 +176,13 @@ extern "C" cc_status cc_graph_reorder(cc_graph* g, int method) {
     int32_t* deg = nullptr;
     void* tmp = nullptr;
     size_t tmp_bytes = 0;
+    uint32_t* hubs = nullptr;
+    int hub_k = 0;
+    const bool lowdeg = method != CC_REORDER_SRC;
     const int grid = cc::device_sms() * 8;
     RCUDA(cc::dmalloc(reinterpret_cast<void**>(&k_out), (size_t)m * sizeof(uint32_t), s));
     RCUDA(cc::dmalloc(reinterpret_cast<void**>(&v_out), (size_t)m * sizeof(uint32_t), s));
-    if (method == CC_REORDER_LOWDEG) {
+    if (lowdeg) {
         RCUDA(cc::dmalloc(reinterpret_cast<void**>(&k_in), (size_t)m * sizeof(uint32_t), s));
         RCUDA(cc::dmalloc(reinterpret_cast<void**>(&v_in), (size_t)m * sizeof(uint32_t), s));
         RCUDA(cc::dmalloc(reinterpret_cast<void**>(&deg), (size_t)n * sizeof(int32_t), s));
@@ -107,6 +201,10 @@ extern "C" cc_status cc_graph_reorder(cc_graph* g, int method) {
     RCUDA(cub::DeviceRadixSort::SortPairs(tmp, tmp_bytes, k_in, k_out, v_in, v_out, (long long)m, 0,
                                           bits_for(n), s));
     RCUDA(cudaStreamSynchronize(s));
+    if (method == CC_REORDER_HUB) {
+        st = select_and_encode_hubs(deg, n, v_out, m, s, &hubs, &hub_k);
+        if (st != CC_OK) goto done;
+    }
     {
         // the sorted pairs must be a permutation of the oriented input: check
         // that every id is in range before the handle gathers with them
@@ -114,7 +212,7 @@ extern "C" cc_status cc_graph_reorder(cc_graph* g, int method) {
         unsigned long long bad = 0;
         RCUDA(cc::dmalloc(reinterpret_cast<void**>(&d_bad), sizeof bad, s));
         RCUDA(cudaMemsetAsync(d_bad, 0, sizeof bad, s));
-        range_check_kernel<<<grid, 256, 0, s>>>(k_out, v_out, m, n, d_bad);
+        range_check_kernel<<<grid, 256, 0, s>>>(k_out, v_out, m, n, hub_k, d_bad);
         cudaError_t e2 = cudaGetLastError();
         if (e2 == cudaSuccess) e2 = cudaMemcpyAsync(&bad, d_bad, sizeof bad, cudaMemcpyDeviceToHost, s);
         if (e2 == cudaSuccess) e2 = cudaStreamSynchronize(s);
@@ -126,9 +224,16 @@ extern "C" cc_status cc_graph_reorder(cc_graph* g, int method) {
         }
     }
     st = cc::graph_replace_edges(g, k_out, v_out);
-    if (st == CC_OK) k_out = v_out = nullptr;  // now owned by the handle
+    if (st == CC_OK) {
+        k_out = v_out = nullptr;  // now owned by the handle
+        if (hub_k > 0) {
+            cc::graph_set_hubs(g, reinterpret_cast<int32_t*>(hubs), hub_k);
+            hubs = nullptr;
+        }
+    }
 done:
-    if (method == CC_REORDER_LOWDEG) {
+    cc::dfree(hubs, s);
+    if (lowdeg) {
         cc::dfree(k_in, s);
         cc::dfree(v_in, s);
     }

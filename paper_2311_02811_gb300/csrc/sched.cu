@@ -34,6 +34,8 @@
 
 #include "../../include/contour.h"
 #include "cc_internal.h"
+#include "csr_kernels.cuh"
+#include "hub_kernels.cuh"
 
 namespace {
 
@@ -311,9 +313,12 @@ __device__ __forceinline__ uint32_t* cl_word(cgx::cluster_group& cl, ClusterSmem
     return &cl.map_shared_rank(me, slot >> kPartBits)->word[slot & (kPart - 1)];
 }
 
+// m_feat < 0: the sample is taken from the m = off_e[1] - off_e[0] edges
+// src/dst.  m_feat >= 0: src/dst already hold the S sampled pairs (S =
+// off_e[1] - off_e[0] <= kSample) of a graph with m_feat edges.
 __global__ void __launch_bounds__(kFeatThreads) features_cluster_kernel(const int64_t* off_v, const int64_t* off_e,
                                                                      const int32_t* src, const int32_t* dst,
-                                                                     float* out) {
+                                                                     long long m_feat, float* out) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     ClusterSmem* me = reinterpret_cast<ClusterSmem*>(smem_raw);
     cgx::cluster_group cl = cgx::this_cluster();
@@ -321,8 +326,9 @@ __global__ void __launch_bounds__(kFeatThreads) features_cluster_kernel(const in
     ClusterSmem* r0 = cl.map_shared_rank(me, 0);
     const long long n = off_v[1] - off_v[0];
     const long long e0 = off_e[0];
-    const long long m = off_e[1] - e0;
-    const long long S = m < kSample ? m : kSample;
+    const bool pre = m_feat >= 0;
+    const long long m = pre ? m_feat : off_e[1] - e0;
+    const long long S = pre ? off_e[1] - e0 : (m < kSample ? m : kSample);
     const long long per = (S + kCl - 1) / kCl;
     const long long jb = rank * per;
     const long long je = min(S, jb + per);
@@ -341,7 +347,7 @@ __global__ void __launch_bounds__(kFeatThreads) features_cluster_kernel(const in
     cl.sync();
     // this CTA's share of the sample: slots and degrees
     for (long long j = jb + threadIdx.x; j < je; j += blockDim.x) {
-        const long long e = e0 + sample_pos(j, m, S);
+        const long long e = e0 + (pre ? j : sample_pos(j, m, S));
         const int32_t pu = cl_slot(cl, me, src[e]);
         const int32_t pv = cl_slot(cl, me, dst[e]);
         me->su[j - jb] = pu;
@@ -737,7 +743,8 @@ cc_status ctx_get(cc::SchedCtx** slot, int32_t G, const int64_t* off_v, const in
 }
 
 // Features of every graph of the context into c->d_feat (caller holds g_mu).
-cc_status run_features(cc::SchedCtx* c, const int32_t* src, const int32_t* dst, cudaStream_t s) {
+cc_status run_features(cc::SchedCtx* c, const int32_t* src, const int32_t* dst, cudaStream_t s,
+                       long long m_feat = -1) {
     if (c->G == 0) return CC_OK;
     if (c->G == 1) {  // one graph: a cluster of 8 CTAs
         SCUDA(cudaMemcpyAsync(c->d_off, c->h_off.data(), 4 * sizeof(int64_t), cudaMemcpyHostToDevice, s));
@@ -760,7 +767,7 @@ cc_status run_features(cc::SchedCtx* c, const int32_t* src, const int32_t* dst, 
         cfg.attrs = attr;
         cfg.numAttrs = 1;
         SCUDA(cudaLaunchKernelEx(&cfg, features_cluster_kernel, (const int64_t*)c->d_off,
-                                 (const int64_t*)(c->d_off + 2), src, dst, c->d_feat));
+                                 (const int64_t*)(c->d_off + 2), src, dst, m_feat, c->d_feat));
         return CC_OK;
     }
     const int grid = std::max(1, std::min<int>(c->G, cc::device_sms() * 2));
@@ -794,6 +801,60 @@ cc_status predict_device(const float* d_feats, int32_t G, int32_t* d_cls, float*
 // internal entry points
 // ---------------------------------------------------------------------------
 
+// The feature pass of one handle (caller holds g_mu).  A native CSR handle
+// first gathers kSample entries as (row, column) pairs; for a symmetric input
+// every undirected edge is stored twice, so its edge count is nnz / 2.
+static cc_status handle_features(cc_graph* g, cudaStream_t s) {
+    long long n = 0, m = 0;
+    cc::graph_nm(g, &n, &m);
+    cc::SchedCtx** slot = cc::graph_sched_slot(g);
+    const int layout = cc::graph_layout(g);
+    if (layout == CC_COO && cc::graph_hub_count(g) > 0) {  // hub-encoded edges: decode a sample
+        const long long S = m < kSample ? m : kSample;
+        const int64_t ov[2] = {0, n}, oe[2] = {0, S};
+        cc_status st = ctx_get(slot, 1, ov, oe, s);
+        if (st != CC_OK) return st;
+        int32_t* pairs = nullptr;
+        SCUDA(cc::dmalloc(reinterpret_cast<void**>(&pairs), (size_t)(2 * S + 1) * sizeof(int32_t), s));
+        cc::hub_sample_kernel<<<(int)((S + 255) / 256), 256, 0, s>>>(
+            static_cast<const int32_t*>(cc::graph_src(g)), static_cast<const int32_t*>(cc::graph_dst(g)), m, S,
+            cc::graph_hubs(g), pairs, pairs + S);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) {
+            cc::dfree(pairs, s);
+            return cc::cuda_fail(e, "hub_sample_kernel", __FILE__, __LINE__);
+        }
+        st = run_features(*slot, pairs, pairs + S, s, m);
+        cc::dfree(pairs, s);
+        return st;
+    }
+    if (layout == CC_COO) {
+        const int64_t ov[2] = {0, n}, oe[2] = {0, m};
+        cc_status st = ctx_get(slot, 1, ov, oe, s);
+        if (st != CC_OK) return st;
+        return run_features(*slot, static_cast<const int32_t*>(cc::graph_src(g)),
+                            static_cast<const int32_t*>(cc::graph_dst(g)), s);
+    }
+    const long long S = m < kSample ? m : kSample;
+    const int64_t ov[2] = {0, n}, oe[2] = {0, S};
+    cc_status st = ctx_get(slot, 1, ov, oe, s);
+    if (st != CC_OK) return st;
+    int32_t* pairs = nullptr;
+    SCUDA(cc::dmalloc(reinterpret_cast<void**>(&pairs), (size_t)(2 * S + 1) * sizeof(int32_t), s));
+    if (S > 0) {
+        cc::csr_sample_kernel<<<(int)((S + 255) / 256), 256, 0, s>>>(
+            cc::graph_csr_off(g), static_cast<const int32_t*>(cc::graph_dst(g)), n, m, S, pairs, pairs + S);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) {
+            cc::dfree(pairs, s);
+            return cc::cuda_fail(e, "csr_sample_kernel", __FILE__, __LINE__);
+        }
+    }
+    st = run_features(*slot, pairs, pairs + S, s, layout == CC_CSR_NATIVE_SYM ? m / 2 : m);
+    cc::dfree(pairs, s);
+    return st;
+}
+
 namespace cc {
 
 cc_status resolve_schedule(cc_graph* g, int* order, int* mode, int* c) {
@@ -805,8 +866,6 @@ cc_status resolve_schedule(cc_graph* g, int* order, int* mode, int* c) {
         *c = want_c < 1 ? 1 : want_c;
         return CC_OK;
     }
-    long long n = 0, m = 0;
-    graph_nm(g, &n, &m);
     if (graph_id_bits(g) != 32) {  // the feature kernel reads int32 ids
         *order = CC_ORDER_FULL;
         *mode = CC_ASYNC;
@@ -814,15 +873,13 @@ cc_status resolve_schedule(cc_graph* g, int* order, int* mode, int* c) {
         return CC_OK;
     }
     cudaStream_t s = graph_stream(g);
-    const int64_t ov[2] = {0, n}, oe[2] = {0, m};
     SchedCtx** slot = graph_sched_slot(g);
-    cc_status st = ctx_get(slot, 1, ov, oe, s);
-    if (st != CC_OK) return st;
-    SchedCtx* x = *slot;
     // the edges of a handle never change: the choice is made once per model
-    if (x->version != g_model_version) {
-        st = run_features(x, static_cast<const int32_t*>(graph_src(g)), static_cast<const int32_t*>(graph_dst(g)), s);
-        if (st == CC_OK) st = predict_device(x->d_feat, 1, x->d_cls, nullptr, s);
+    if (!*slot || (*slot)->version != g_model_version) {
+        cc_status st = handle_features(g, s);
+        if (st != CC_OK) return st;
+        SchedCtx* x = *slot;
+        st = predict_device(x->d_feat, 1, x->d_cls, nullptr, s);
         if (st == CC_OK) {
             cudaError_t e = cudaMemcpyAsync(x->h_cls.data(), x->d_cls, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
             if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -832,7 +889,7 @@ cc_status resolve_schedule(cc_graph* g, int* order, int* mode, int* c) {
         x->version = g_model_version;
     }
     int cc_ = 1;
-    decode(x->h_cls[0], order, mode, &cc_);
+    decode((*slot)->h_cls[0], order, mode, &cc_);
     *c = want_c >= 1 ? want_c : cc_;
     return CC_OK;
 }
@@ -908,14 +965,9 @@ extern "C" cc_status cc_graph_features(cc_graph* g, float* features_out) {
     if (cc::graph_id_bits(g) != 32) return cc::set_error(CC_EINVAL, "cc_graph_features: int32 ids only");
     // the feature scratch is shared: each use completes before the lock is released
     std::lock_guard<std::mutex> lock(g_mu);
-    long long n = 0, m = 0;
-    cc::graph_nm(g, &n, &m);
     cudaStream_t s = cc::graph_stream(g);
-    const int64_t ov[2] = {0, n}, oe[2] = {0, m};
     cc::SchedCtx** slot = cc::graph_sched_slot(g);
-    cc_status st = ctx_get(slot, 1, ov, oe, s);
-    if (st != CC_OK) return st;
-    st = run_features(*slot, static_cast<const int32_t*>(cc::graph_src(g)), static_cast<const int32_t*>(cc::graph_dst(g)), s);
+    cc_status st = handle_features(g, s);
     if (st != CC_OK) return st;
     cudaError_t e = cudaMemcpyAsync(features_out, (*slot)->d_feat, kFeat * sizeof(float), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);

@@ -277,7 +277,7 @@ def test_grid4096_full_size(cc):
         assert (got == want).all(), (order, mode)
 
 
-@pytest.mark.parametrize("method", [1, 2], ids=["src", "lowdeg"])
+@pytest.mark.parametrize("method", [1, 2, 3], ids=["src", "lowdeg", "hub"])
 def test_reorder_keeps_labels_and_sync_sequence(cc, method):
     """Edge order is a layout choice: labels (and, in sync mode, every state
     and the sweep count) are those of the original edge list."""
@@ -363,3 +363,32 @@ def test_non_default_streams_and_concurrent_handles(cc):
     assert (outs[0].cpu().numpy() == wants[0]).all()
     for h in handles:
         cc.cc_free(h)
+
+
+@pytest.mark.parametrize("layout", ["coo", "hub", "csr"])
+def test_host_polled_launch_matches_graph_launch(cc, layout):
+    """CC_LAUNCH_HOST runs the same blocks from the host: identical labels,
+    sweep counts and (sync, stopped early) intermediate states."""
+    n, s, d = SMALL["rmat12"](7)
+    if layout == "csr":
+        off, cols = gg.to_csr(n, s, d, symmetric=True)
+        g = cc.cc_init(n, off.cuda(), cols.cuda(), m=cols.numel(), id_bits=32,
+                       layout=cc.CC_CSR_NATIVE_SYM, on_device=True)
+    else:
+        g = cc.cc_init(n, s.cuda(), d.cuda())
+        if layout == "hub":
+            cc.cc_graph_reorder(g, cc.CC_REORDER_HUB)
+    want = oracle.uf_labels(n, s, d)
+    _, it, _, states = oracle.contour_sync(n, s, d, 2, record=True)
+    out = torch.empty(n, dtype=torch.int32, device="cuda")
+    for launch in (cc.CC_LAUNCH_HOST, cc.CC_LAUNCH_GRAPH, cc.CC_LAUNCH_HOST):
+        cc.cc_graph_set_launch(g, launch)
+        for order, mode, c in [(2, cc.CC_ASYNC, 1), (0, cc.CC_ASYNC, 2), (cc.CC_ORDER_1M1M, cc.CC_ASYNC, 1)]:
+            cc.cc_run(g, out, order, mode, c)
+            assert (out.cpu().numpy() == want).all(), (launch, order, mode, c)
+        for k in (1, 2, it):
+            rc, st = cc.cc_run(g, out, 2, cc.CC_SYNC, 1, max_sweeps=k, raise_on_error=False)
+            assert st.sweeps == k and (out.cpu().numpy() == states[k - 1]).all(), (launch, k)
+    with pytest.raises(cc.CCError):
+        cc.cc_graph_set_launch(g, 7)
+    cc.cc_free(g)

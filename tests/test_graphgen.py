@@ -1,4 +1,5 @@
 """The seeded input generators (no GPU): sizes, structure and determinism."""
+import pytest
 import numpy as np
 import torch
 
@@ -73,3 +74,18 @@ def test_family_sizes():
         assert n == p["n"]
         if b > a:
             assert int(s[a:b].max()) < n and int(d[a:b].max()) < n
+
+
+@pytest.mark.parametrize("symmetric", [False, True])
+def test_to_csr_matches_sorted_entries(symmetric):
+    n, s, d = 300, *gg.er(300, 900, seed=21)
+    s = torch.cat([s, torch.tensor([5, 7], dtype=torch.int32)])  # a loop and a repeat
+    d = torch.cat([d, torch.tensor([5, int(d[0])], dtype=torch.int32)])
+    off, cols = gg.to_csr(n, s, d, symmetric=symmetric)
+    sn, dn = s.numpy().astype(np.int64), d.numpy().astype(np.int64)
+    rows = np.concatenate([sn, dn]) if symmetric else sn
+    want_cols = np.concatenate([dn, sn]) if symmetric else dn
+    order = np.argsort(rows, kind="stable")
+    assert off.dtype == torch.int64 and off[0] == 0 and off[-1] == rows.size
+    assert np.array_equal(np.diff(off.numpy()), np.bincount(rows, minlength=n))
+    assert np.array_equal(cols.numpy(), want_cols[order])
