@@ -25,6 +25,7 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+import numpy as np  # noqa: E402
 import torch  # noqa: E402
 
 import graphgen as gg  # noqa: E402
@@ -519,10 +520,19 @@ def batch_compare(cc, G, args, dev, stream, seed):
         res[name] = {"ms": ms, "first_call_ms": first, "edges_per_s": total_m / (ms * 1e-3)}
     ref = out_b.clone()
     learned = os.path.exists(cc.SCHED_WEIGHTS_PATH)
+    per_kind = None
     if learned:
         cc.load_default_scheduler()
         first = ev_ms(lambda: cc.cc_batch_run(plan, out_b, cc.CC_ORDER_AUTO, cc.CC_ASYNC, 0), 1)
         ms = ev_ms(lambda: cc.cc_batch_run(plan, out_b, cc.CC_ORDER_AUTO, cc.CC_ASYNC, 0), reps)
+        sweeps = np.asarray(cc.cc_batch_run(plan, out_b, cc.CC_ORDER_AUTO, cc.CC_ASYNC, 0)[0])
+        kinds = np.array([p["kind"] for p in params])
+        ns, ms_ = np.diff(vo), np.diff(eo)
+        budget = cc.cc_batch_tuning(plan)[0]
+        per_kind = {k: {"graphs": int((kinds == k).sum()), "edges": int(ms_[kinds == k].sum()),
+                        "in_shared_memory": int(((kinds == k) & (ns * 4 <= budget)).sum()),
+                        "sweeps_mean": float(sweeps[kinds == k].mean()), "sweeps_max": int(sweeps[kinds == k].max())}
+                    for k in sorted(set(kinds.tolist()))}
         res["batched-learned"] = {"ms": ms, "first_call_ms": first, "edges_per_s": total_m / (ms * 1e-3),
                                   "note": "first call includes the feature pass and inference"}
         identical_learned = bool(torch.equal(out_b, ref))
@@ -550,7 +560,7 @@ def batch_compare(cc, G, args, dev, stream, seed):
     tuning = cc.cc_batch_tuning(plan)
     cc.cc_batch_free(plan)
     best_batched = "batched-learned" if learned else "batched-c2-async"
-    return {"workload": f"batch-mix-{G}", "graphs": G, "n": total_n, "m": total_m,
+    return {"workload": f"batch-mix-{G}", "graphs": G, "n": total_n, "m": total_m, "per_kind_learned": per_kind,
             "generation_s": gen_s, "plan_and_autotune_s": tune_s,
             "edge_order": ("as generated (shuffled)" if reorder_s is None else
                            f"cc_batch_reorder once before timing ({reorder_s:.2f} s); the plain "
