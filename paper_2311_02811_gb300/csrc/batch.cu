@@ -313,8 +313,16 @@ __global__ void __launch_bounds__(kLargeThreads) batch_round_kernel(Dev d, int c
     int i = find_tile(d.tpre[cls], cnt, t_begin);
     long long t0 = d.tpre[cls][i], t1 = d.tpre[cls][i + 1];
     int32_t g = d.act[cls][i];
+    // the flag of graph g is raised once per warp and graph span, not per
+    // tile: per-tile stores from every warp to the same word serialise in L2
+    bool pending = false;
+    auto flush = [&](int32_t gg) {
+        if (__any_sync(0xffffffffu, pending) && lane == 0 && ((round + 1) % d.c[gg]) == 0) d.flag[gg] = 1;
+        pending = false;
+    };
     for (long long t = t_begin; t < t_end; ++t) {
         while (t >= t1) {
+            flush(g);
             ++i;
             t0 = t1;
             t1 = d.tpre[cls][i + 1];
@@ -325,7 +333,6 @@ __global__ void __launch_bounds__(kLargeThreads) batch_round_kernel(Dev d, int c
         int32_t* L = d.L + d.off_v[g];
         const bool sync = d.sync[g] != 0;
         int32_t* Lu = sync ? d.Lu + d.off_v[g] : nullptr;
-        const bool checked = ((round + 1) % d.c[g]) == 0;
         // edges of this lane; lanes past the graph's end take the self-loop
         // <0, 0>, which never writes (L[0] = 0 always holds)
         int32_t w[kEPT], v[kEPT];
@@ -347,8 +354,9 @@ __global__ void __launch_bounds__(kLargeThreads) batch_round_kernel(Dev d, int c
             const int h = d.h[g];
             viol = sync ? cc::mm_runtime_ilp<true, kEPT>(w, v, h, L, Lu) : cc::mm_runtime_ilp<false, kEPT>(w, v, h, L, Lu);
         }
-        if (__any_sync(0xffffffffu, viol) && lane == 0 && checked) d.flag[g] = 1;
+        pending |= viol;
     }
+    flush(g);
 }
 
 // L = L_u for the vertices of active synchronous large graphs (Alg. 1 copy).

@@ -256,13 +256,10 @@ static cudaError_t launch_sweep_t(const cc_graph* g, IdT* L, IdT* Lu, int h, int
         if (g->hub_k > 0) {
             auto kh = cc::mm_sweep_hub_kernel<H, SYNC>;
             const size_t smem = (size_t)g->hub_k * 2 * sizeof(int32_t);
-            static bool attr = false;
-            if (!attr) {
-                cudaError_t e = cudaFuncSetAttribute(kh, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                     cc::kHubMax * 2 * (int)sizeof(int32_t));
-                if (e != cudaSuccess) return e;
-                attr = true;
-            }
+            // per device and cheap: set before every launch (or capture)
+            cudaError_t e = cudaFuncSetAttribute(kh, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 cc::kHubMax * 2 * (int)sizeof(int32_t));
+            if (e != cudaSuccess) return e;
             kh<<<cc::device_sms(), cc::kHubThreads, smem, s>>>(
                 static_cast<const int32_t*>(g->src), static_cast<const int32_t*>(g->dst), g->m, L, Lu, h, flag,
                 g->ctl, first, gate, g->hubs, g->hub_k);

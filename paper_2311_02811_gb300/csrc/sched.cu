@@ -748,12 +748,9 @@ cc_status run_features(cc::SchedCtx* c, const int32_t* src, const int32_t* dst, 
     if (c->G == 0) return CC_OK;
     if (c->G == 1) {  // one graph: a cluster of 8 CTAs
         SCUDA(cudaMemcpyAsync(c->d_off, c->h_off.data(), 4 * sizeof(int64_t), cudaMemcpyHostToDevice, s));
-        static bool attr_set = false;
-        if (!attr_set) {
-            SCUDA(cudaFuncSetAttribute(features_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)sizeof(ClusterSmem)));
-            attr_set = true;
-        }
+        // per device and cheap: set before every launch
+        SCUDA(cudaFuncSetAttribute(features_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)sizeof(ClusterSmem)));
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(kCl, 1, 1);
         cfg.blockDim = dim3(kFeatThreads, 1, 1);
