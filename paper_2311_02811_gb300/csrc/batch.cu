@@ -19,12 +19,13 @@
 //    (Section III-B2), retires converged graphs and rebuilds the active
 //    lists and tile prefix sums for the next round.
 //    The large graphs are split into waves whose labels together fit in L2
-//    (kWaveBytes); a wave runs until all its graphs have converged, then the
-//    next one starts.  Every graph still runs its own iteration from its own
-//    first sweep, so waves change nothing but which graphs share a round:
-//    with all large graphs in one round, their labels (gigabytes for a big
-//    batch) would not stay in L2 and every scattered label gather would go
-//    to DRAM.
+//    (kWaveBytes); the next wave is admitted once the active work left falls
+//    below what keeps the grid busy (a wave's last rounds hold only its
+//    slowest graphs).  Every graph still runs its own iteration from its own
+//    first sweep (its start round is recorded), so waves change nothing but
+//    which graphs share a round: with all large graphs in one round, their
+//    labels (gigabytes for a big batch) would not stay in L2 and every
+//    scattered label gather would go to DRAM.
 // No kernel waits on another CTA; rounds are separated by kernel boundaries.
 #include <cub/device/device_radix_sort.cuh>
 #include <cuda_runtime.h>
@@ -67,9 +68,9 @@ int order_class(int order) {
 
 struct BatchCtl {
     int32_t round;       // rounds completed
-    int32_t wave;        // current wave of large graphs
+    int32_t wave;        // last wave of large graphs admitted
     int32_t n_waves;
-    int32_t wave_start;  // rounds completed when the current wave started
+    long long admit_tiles;  // admit the next wave while fewer tiles are active
     int32_t max_sweeps;
     int32_t small_next;  // queue head of the small-graph kernel
     int32_t sact_cnt;    // active synchronous large graphs
@@ -98,6 +99,7 @@ struct Dev {
     int32_t* sweeps;
     int32_t* state;
     const int32_t* wave;  // wave of each large graph
+    int32_t* start;       // rounds completed when the graph's wave was admitted
     // small graphs
     const int32_t* small_list;
     int32_t n_small;
@@ -180,8 +182,8 @@ __device__ void rebuild_lists(const Dev& d, bool setup) {
             const int32_t i = base + threadIdx.x;
             int32_t g = -1;
             if (i < cnt) g = srcl[i];
-            // the static lists hold every large graph: take the current wave's
-            const bool keep = g >= 0 && d.state[g] == kActive && (!setup || d.wave[g] == d.ctl->wave);
+            // the static lists hold every large graph: take the admitted waves'
+            const bool keep = g >= 0 && d.state[g] == kActive && (!setup || d.wave[g] <= d.ctl->wave);
             __syncthreads();  // every read of this chunk precedes the writes below
             int32_t kept_total;
             const int32_t pos = block_exclusive_scan<int32_t>(keep ? 1 : 0, &kept_total, shi);
@@ -227,12 +229,35 @@ __device__ void rebuild_lists(const Dev& d, bool setup) {
     }
 }
 
-__global__ void __launch_bounds__(kCheckThreads) batch_setup_kernel(Dev d, int32_t max_sweeps, int32_t n_waves) {
+// While the active large graphs hold fewer than admit_tiles tiles, admit the
+// next wave: its graphs start counting sweeps at round `done`.
+__device__ void admit_waves(const Dev& d, int32_t done) {
+    __shared__ int admit;
+    for (int iter = 0; iter < (1 << 20); ++iter) {  // ends: each pass admits one of finitely many waves
+        if (threadIdx.x == 0) {
+            long long tiles = 0;
+            for (int k = 0; k < kClasses; ++k) tiles += d.ctl->tiles[k];
+            admit = tiles < d.ctl->admit_tiles && d.ctl->wave + 1 < d.ctl->n_waves;
+            if (admit) d.ctl->wave += 1;
+        }
+        __syncthreads();
+        if (!admit) break;
+        const int32_t w = d.ctl->wave;
+        for (int32_t g = threadIdx.x; g < d.G; g += blockDim.x)
+            if (d.wave[g] == w) d.start[g] = done;
+        __syncthreads();
+        rebuild_lists(d, true);
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(kCheckThreads) batch_setup_kernel(Dev d, int32_t max_sweeps, int32_t n_waves,
+                                                                   long long admit_tiles) {
     if (threadIdx.x == 0) {
         d.ctl->round = 0;
         d.ctl->wave = 0;
         d.ctl->n_waves = n_waves;
-        d.ctl->wave_start = 0;
+        d.ctl->admit_tiles = admit_tiles;
         d.ctl->max_sweeps = max_sweeps;
         d.ctl->small_next = 0;
         d.ctl->compress_changes = 0;
@@ -241,19 +266,22 @@ __global__ void __launch_bounds__(kCheckThreads) batch_setup_kernel(Dev d, int32
         d.flag[g] = 0;
         d.sweeps[g] = 0;
         d.state[g] = kActive;
+        d.start[g] = 0;
     }
     __syncthreads();
     rebuild_lists(d, true);
+    __syncthreads();
+    admit_waves(d, 0);
 }
 
 __global__ void __launch_bounds__(kCheckThreads) batch_check_kernel(Dev d, cudaGraphConditionalHandle loop) {
-    const int32_t done = d.ctl->round + 1;          // rounds completed including this one
-    const int32_t round = done - d.ctl->wave_start;  // sweeps of the current wave's graphs
+    const int32_t done = d.ctl->round + 1;  // rounds completed including this one
     const int32_t maxs = d.ctl->max_sweeps;
     for (int k = 0; k < kClasses; ++k) {
         const int32_t cnt = d.ctl->act_cnt[k];
         for (int32_t i = threadIdx.x; i < cnt; i += blockDim.x) {
             const int32_t g = d.act[k][i];
+            const int32_t round = done - d.start[g];  // sweeps of graph g so far
             if (round % d.c[g] == 0) {
                 if (d.flag[g] == 0) {
                     d.state[g] = kConverged;
@@ -270,19 +298,9 @@ __global__ void __launch_bounds__(kCheckThreads) batch_check_kernel(Dev d, cudaG
     }
     __syncthreads();
     rebuild_lists(d, false);
-    __shared__ int next_wave;
-    if (threadIdx.x == 0) {
-        d.ctl->round = done;
-        int any = 0;
-        for (int k = 0; k < kClasses; ++k) any |= d.ctl->act_cnt[k] > 0;
-        next_wave = !any && d.ctl->wave + 1 < d.ctl->n_waves;
-        if (next_wave) {
-            d.ctl->wave += 1;
-            d.ctl->wave_start = done;
-        }
-    }
     __syncthreads();
-    if (next_wave) rebuild_lists(d, true);
+    if (threadIdx.x == 0) d.ctl->round = done;
+    admit_waves(d, done);
     if (threadIdx.x == 0) {
         int any = 0;
         for (int k = 0; k < kClasses; ++k) any |= d.ctl->act_cnt[k] > 0;
@@ -298,7 +316,7 @@ template <int H>
 __global__ void __launch_bounds__(kLargeThreads) batch_round_kernel(Dev d, int cls) {
     const long long total = d.ctl->tiles[cls];
     const int32_t cnt = d.ctl->act_cnt[cls];
-    const int32_t round = d.ctl->round - d.ctl->wave_start;  // sweep index of the wave's graphs
+    const int32_t done = d.ctl->round;  // rounds completed before this one
     // every warp takes an equal, contiguous range of tiles and walks the
     // active graphs along it (one search per warp, then sequential steps).
     // Walking a graph's sorted edges in order lets labels travel far within
@@ -317,7 +335,8 @@ __global__ void __launch_bounds__(kLargeThreads) batch_round_kernel(Dev d, int c
     // tile: per-tile stores from every warp to the same word serialise in L2
     bool pending = false;
     auto flush = [&](int32_t gg) {
-        if (__any_sync(0xffffffffu, pending) && lane == 0 && ((round + 1) % d.c[gg]) == 0) d.flag[gg] = 1;
+        const int32_t r = done - d.start[gg];  // sweep index of graph gg in this round
+        if (__any_sync(0xffffffffu, pending) && lane == 0 && ((r + 1) % d.c[gg]) == 0) d.flag[gg] = 1;
         pending = false;
     };
     for (long long t = t_begin; t < t_end; ++t) {
@@ -333,6 +352,7 @@ __global__ void __launch_bounds__(kLargeThreads) batch_round_kernel(Dev d, int c
         int32_t* L = d.L + d.off_v[g];
         const bool sync = d.sync[g] != 0;
         int32_t* Lu = sync ? d.Lu + d.off_v[g] : nullptr;
+        const int32_t round = done - d.start[g];  // sweep index of graph g
         // edges of this lane; lanes past the graph's end take the self-loop
         // <0, 0>, which never writes (L[0] = 0 always holds)
         int32_t w[kEPT], v[kEPT];
@@ -777,14 +797,14 @@ void destroy_batch(cc_batch_plan* b) {
 
 // Sizes of the per-graph and list regions.
 struct Layout {
-    size_t pg_ints;     // 7 * G
+    size_t pg_ints;     // 8 * G
     size_t list_ints;   // small list + 4 static class lists + 4 active + sact + large_all
     size_t pre_longs;   // 4 tile prefixes + vpre + large_vpre + edge-tile prefix (G+1 each)
 };
 
 Layout layout_for(int32_t G) {
     Layout l;
-    l.pg_ints = 7ull * G;
+    l.pg_ints = 8ull * G;
     l.list_ints = 12ull * (G + 1);
     l.pre_longs = 7ull * (G + 1);
     return l;
@@ -816,6 +836,7 @@ Dev make_dev(const cc_batch_plan* b, int32_t* L, std::vector<int32_t>& lists_h, 
     d.sweeps = b->d_pg + 4 * G;
     d.state = b->d_pg + 5 * G;
     d.wave = b->d_pg + 6 * G;
+    d.start = b->d_pg + 7 * G;
     d.ctl = b->d_ctl;
 
     // host-side classification (lists are uploaded by the caller)
@@ -1026,7 +1047,12 @@ cc_status batch_solve(cc_batch_plan* b, int32_t max_sweeps, int32_t* labels_out,
     }
 
     BCUDA(cudaEventRecord(b->ev0, s));
-    batch_setup_kernel<<<1, kCheckThreads, 0, s>>>(d, max_sweeps, n_waves);
+    // admit waves while the active large graphs hold fewer tiles than 8 per
+    // warp of the round kernels' persistent grid
+    const long long admit_tiles =
+        8ll * (kLargeThreads / 32) *
+        persistent_grid(reinterpret_cast<const void*>(batch_round_kernel<2>), kLargeThreads, 0);
+    batch_setup_kernel<<<1, kCheckThreads, 0, s>>>(d, max_sweeps, n_waves, admit_tiles);
     BCUDA(cudaGetLastError());
     if (n_small > 0) {
         const size_t smem = (size_t)b->small_budget;

@@ -188,3 +188,32 @@ def test_batch_reorder_keeps_every_graph(cc, mix):
         assert sweeps.tolist() == want_sweeps
         _check_labels(vo, out, truth)
     cc.cc_batch_free(b)
+
+
+def test_batch_waves_keep_per_graph_sweeps(cc):
+    """Twenty 10^6-vertex graphs: 80 MB of labels, more than one wave of the
+    large-graph path (a wave holds at most 64 MB of labels).  Each graph's
+    synchronous sweep count is counted from its own first sweep, so it must
+    still equal the Alg. 1 simulator's, and every label the oracle's."""
+    G, n = 20, 1_000_000
+    graphs = [gg.er(n, 2 * n, seed=900 + g) for g in range(G)]
+    vo = np.arange(G + 1, dtype=np.int64) * n
+    eo = np.concatenate([[0], np.cumsum([s.numel() for s, _ in graphs])]).astype(np.int64)
+    s = torch.cat([x for x, _ in graphs]).cuda()
+    d = torch.cat([y for _, y in graphs]).cuda()
+    b = cc.cc_batch_init(vo, eo, s, d)
+    cc.cc_batch_set_tuning(b, 0, 512, 4)  # every graph on the large-graph path
+    out = torch.empty(G * n, dtype=torch.int32, device="cuda")
+    sweeps, _ = cc.cc_batch_run(b, out, 2, cc.CC_SYNC, 1)
+    lab = out.cpu().numpy()
+    for g, (gs, gd) in enumerate(graphs):
+        want, it, conv, _ = oracle.contour_sync(n, gs, gd, 2)
+        assert conv and sweeps[g] == it, (g, sweeps[g], it)
+        assert np.array_equal(lab[g * n:(g + 1) * n], want), g
+    for order in (2, 0):
+        out.fill_(-1)
+        cc.cc_batch_run(b, out, order, cc.CC_ASYNC, 1)
+        lab = out.cpu().numpy()
+        for g, (gs, gd) in enumerate(graphs):
+            assert np.array_equal(lab[g * n:(g + 1) * n], oracle.uf_labels(n, gs, gd)), (order, g)
+    cc.cc_batch_free(b)
