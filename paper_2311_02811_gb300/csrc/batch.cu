@@ -740,6 +740,8 @@ struct cc_batch_plan {
     bool own_edges = false;  // after cc_batch_reorder
     cudaStream_t stream = nullptr;
     cudaStream_t cap = nullptr;
+    cudaStream_t aux[kClasses - 1] = {};  // capture branches for concurrent class kernels
+    cudaEvent_t fork = nullptr, join[kClasses] = {};
     // device buffers
     int64_t* d_off_v = nullptr;
     int64_t* d_off_e = nullptr;
@@ -790,6 +792,11 @@ void destroy_batch(cc_batch_plan* b) {
     cudaFree(b->d_Lu);
     if (b->h_ctl) cudaFreeHost(b->h_ctl);
     if (b->cap) cudaStreamDestroy(b->cap);
+    for (auto& a : b->aux)
+        if (a) cudaStreamDestroy(a);
+    if (b->fork) cudaEventDestroy(b->fork);
+    for (auto& j : b->join)
+        if (j) cudaEventDestroy(j);
     if (b->ev0) cudaEventDestroy(b->ev0);
     if (b->ev1) cudaEventDestroy(b->ev1);
     delete b;
@@ -956,17 +963,32 @@ cc_status build_loop(cc_batch_plan* b, const Dev& d, BatchLoop* out) {
         const int g2 = persistent_grid(reinterpret_cast<const void*>(batch_round_kernel<2>), kLargeThreads, 0);
         const int g4 = persistent_grid(reinterpret_cast<const void*>(batch_round_kernel<4>), kLargeThreads, 0);
         const int g0 = persistent_grid(reinterpret_cast<const void*>(batch_round_kernel<0>), kLargeThreads, 0);
-        int32_t present[kClasses] = {d.large_cls_cnt[0], d.large_cls_cnt[1], d.large_cls_cnt[2], d.large_cls_cnt[3]};
-        if (present[0]) batch_round_kernel<1><<<g1, kLargeThreads, 0, b->cap>>>(d, 0);
-        if (present[1]) batch_round_kernel<2><<<g2, kLargeThreads, 0, b->cap>>>(d, 1);
-        if (present[2]) batch_round_kernel<4><<<g4, kLargeThreads, 0, b->cap>>>(d, 2);
-        if (present[3]) batch_round_kernel<0><<<g0, kLargeThreads, 0, b->cap>>>(d, 3);
+        // the order classes touch disjoint graphs: their kernels are parallel
+        // branches of the round (joined before the copy and the check)
+        cudaStream_t branch[kClasses];
+        int used = 0;
+        cudaError_t eb = cudaEventRecord(b->fork, b->cap);
+        auto next_stream = [&]() {
+            cudaStream_t st = used == 0 ? b->cap : b->aux[used - 1];
+            if (used > 0 && eb == cudaSuccess) eb = cudaStreamWaitEvent(st, b->fork, 0);
+            branch[used++] = st;
+            return st;
+        };
+        if (d.large_cls_cnt[0]) batch_round_kernel<1><<<g1, kLargeThreads, 0, next_stream()>>>(d, 0);
+        if (d.large_cls_cnt[1]) batch_round_kernel<2><<<g2, kLargeThreads, 0, next_stream()>>>(d, 1);
+        if (d.large_cls_cnt[2]) batch_round_kernel<4><<<g4, kLargeThreads, 0, next_stream()>>>(d, 2);
+        if (d.large_cls_cnt[3]) batch_round_kernel<0><<<g0, kLargeThreads, 0, next_stream()>>>(d, 3);
+        for (int i = 1; i < used && eb == cudaSuccess; ++i) {
+            eb = cudaEventRecord(b->join[i], branch[i]);
+            if (eb == cudaSuccess) eb = cudaStreamWaitEvent(b->cap, b->join[i], 0);
+        }
         if (d.Lu) {
             const int gc = persistent_grid(reinterpret_cast<const void*>(batch_sync_copy_kernel), 256, 0);
             batch_sync_copy_kernel<<<gc, 256, 0, b->cap>>>(d);
         }
         batch_check_kernel<<<1, kCheckThreads, 0, b->cap>>>(d, handle);
         cudaError_t ek = cudaGetLastError();
+        if (ek == cudaSuccess) ek = eb;
         cudaGraph_t captured = nullptr;
         e = cudaStreamEndCapture(b->cap, &captured);
         if (ek != cudaSuccess) e = ek;
@@ -1254,6 +1276,11 @@ extern "C" cc_status cc_batch_init(cc_batch_plan** out, int32_t n_graphs, const 
     if (e == cudaSuccess) e = cudaMalloc(&b->d_ctl, sizeof(BatchCtl));
     if (e == cudaSuccess) e = cudaMallocHost(&b->h_ctl, sizeof(BatchCtl));
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
+    for (auto& a : b->aux)
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&a, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+    for (auto& j : b->join)
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&j, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreate(&b->ev0);
     if (e == cudaSuccess) e = cudaEventCreate(&b->ev1);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(batch_small_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
