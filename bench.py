@@ -438,7 +438,8 @@ def variants(cc, g, out, n, m, args, dev, seed, stream, s=None, d=None):
     for order, mode, name in [(2, cc.CC_SYNC, "o2-sync"), (4, cc.CC_ASYNC, "o4-async"),
                               (4, cc.CC_SYNC, "o4-sync"), (0, cc.CC_ASYNC, "full-async"),
                               (1, cc.CC_ASYNC, "o1-async"), (cc.CC_ORDER_11MM, cc.CC_ASYNC, "c11mm-async"),
-                              (cc.CC_ORDER_1M1M, cc.CC_ASYNC, "c1m1m-async")]:
+                              (cc.CC_ORDER_1M1M, cc.CC_ASYNC, "c1m1m-async"),
+                              (0, cc.CC_ASYNC_COMPACT, "full-compact")]:
         res[f"{args.workload}/{name}"] = measure(g, out, n, m, order, mode, 1)
     if os.path.exists(cc.SCHED_WEIGHTS_PATH):
         cc.load_default_scheduler()
@@ -468,7 +469,8 @@ def variants(cc, g, out, n, m, args, dev, seed, stream, s=None, d=None):
         g2 = cc.cc_init(n2, s2, d2, stream=stream.cuda_stream)
         o2 = torch.empty(n2, dtype=torch.int32, device=dev)
         for order, mode, name in [(2, cc.CC_ASYNC, "o2-async"), (2, cc.CC_SYNC, "o2-sync"),
-                                  (4, cc.CC_ASYNC, "o4-async"), (0, cc.CC_ASYNC, "full-async")]:
+                                  (4, cc.CC_ASYNC, "o4-async"), (0, cc.CC_ASYNC, "full-async"),
+                                  (0, cc.CC_ASYNC_COMPACT, "full-compact")]:
             res[f"grid4096/{name}"] = measure(g2, o2, n2, s2.numel(), order, mode, 1)
         cc.cc_free(g2)
     return res

@@ -49,7 +49,14 @@ typedef enum {
 
 enum { CC_ID32 = 32, CC_ID64 = 64 };
 enum { CC_COO = 0, CC_CSR = 1, CC_CSR_NATIVE = 2, CC_CSR_NATIVE_SYM = 3 };
-enum { CC_SYNC = 0, CC_ASYNC = 1 };
+/* CC_ASYNC_COMPACT: asynchronous full-chain sweeps (order CC_ORDER_FULL only)
+ * that drop every edge whose two chain walks ended at the same root: with the
+ * full chain a tree never splits, so such an edge can never lower a label
+ * again, and the final compress (every label set to the root of its chain)
+ * gives its endpoints the same label.  Later sweeps read only the edges kept.
+ * int32 edge lists only (no native CSR, no hub layout); the handle allocates
+ * two more edge lists of its size on first use. */
+enum { CC_SYNC = 0, CC_ASYNC = 1, CC_ASYNC_COMPACT = 2 };
 /* Operator order: h >= 1 is MM^h of Def. 3; CC_ORDER_FULL follows each label
  * chain to its root (at most 1024 hops, the "C-m" variant with m = 1024 of
  * Section III-B4); CC_ORDER_AUTO lets the learned scheduler choose. */
@@ -132,6 +139,7 @@ cc_status cc_init(cc_graph **g, int64_t n, int id_bits, int layout, const void *
  *                   writes into the update array L_u (Eq. "cas"), then L = L_u;
  *                   every sweep is deterministic.  CC_ASYNC: in-place plain
  *                   stores into L (Section III-B1 and III-B3).
+ *                   CC_ASYNC_COMPACT: CC_ASYNC with edge compaction (above).
  *   check_interval  c >= 1: the convergence flag of Section III-B2 is taken
  *                   from the last sweep of every block of c sweeps; the run
  *                   stops after the first block whose last sweep saw no edge

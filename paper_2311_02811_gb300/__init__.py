@@ -17,7 +17,7 @@ import os
 __all__ = [
     "CC_OK", "CC_EINVAL", "CC_EIDRANGE", "CC_ENOMEM", "CC_ECUDA", "CC_ENOTCONVERGED",
     "CC_ETIMEOUT", "CC_ID32", "CC_ID64", "CC_COO", "CC_CSR", "CC_CSR_NATIVE", "CC_CSR_NATIVE_SYM",
-    "CC_SYNC", "CC_ASYNC",
+    "CC_SYNC", "CC_ASYNC", "CC_ASYNC_COMPACT",
     "CC_ORDER_FULL", "CC_ORDER_AUTO", "CC_ORDER_11MM", "CC_ORDER_1M1M", "CC_NOALLOC_MAX_N", "CCError", "cc_stats", "cc_graph", "lib", "LIB_PATH",
     "cc_init", "cc_run", "cc_run_noalloc", "cc_free", "cc_release_memory", "cc_batch_plan", "cc_batch_init",
     "cc_batch_run", "cc_batch_set_schedule", "cc_batch_run_scheduled", "cc_batch_tuning",
@@ -32,7 +32,7 @@ LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libcontour.
 CC_OK, CC_EINVAL, CC_EIDRANGE, CC_ENOMEM, CC_ECUDA, CC_ENOTCONVERGED, CC_ETIMEOUT = range(7)
 CC_ID32, CC_ID64 = 32, 64
 CC_COO, CC_CSR, CC_CSR_NATIVE, CC_CSR_NATIVE_SYM = 0, 1, 2, 3
-CC_SYNC, CC_ASYNC = 0, 1
+CC_SYNC, CC_ASYNC, CC_ASYNC_COMPACT = 0, 1, 2
 CC_ORDER_FULL, CC_ORDER_AUTO = 0, -1
 CC_ORDER_11MM, CC_ORDER_1M1M = -2, -3
 CC_NOALLOC_MAX_N = 4194304

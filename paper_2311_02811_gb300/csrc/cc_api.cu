@@ -24,6 +24,7 @@
 #include "mm_kernels.cuh"
 #include "csr_kernels.cuh"
 #include "hub_kernels.cuh"
+#include "compact_kernels.cuh"
 
 using cc::Ctl;
 
@@ -182,6 +183,7 @@ struct cc_graph {
     int32_t* hubs = nullptr;  // CC_REORDER_HUB: dst entry ~s names hubs[s]
     int hub_k = 0;
     int launch = CC_LAUNCH_GRAPH;  // or CC_LAUNCH_HOST (cc_graph_set_launch)
+    cc::CompactLists clists = {};  // CC_ASYNC_COMPACT: two edge lists + counters (allocated on first use)
     void* L = nullptr;   // working labels when the caller's output is on the host
     void* Lu = nullptr;  // update array of synchronous runs
     Ctl* ctl = nullptr;
@@ -214,6 +216,11 @@ static void destroy(cc_graph* g) {
     if (g->own_off) cc::dfree(g->off, g->stream);
     cc::dfree(g->seg, g->stream);
     cc::dfree(g->hubs, g->stream);
+    for (int i = 0; i < 2; ++i) {
+        cc::dfree(g->clists.src[i], g->stream);
+        cc::dfree(g->clists.dst[i], g->stream);
+    }
+    cc::dfree(g->clists.cnt, g->stream);
     cc::dfree(g->L, g->stream);
     cc::dfree(g->Lu, g->stream);
     cc::dfree(g->ctl, g->stream);
@@ -332,6 +339,26 @@ static cudaError_t enqueue_block(cc_graph* g, int order, int mode, int c, IdT* L
         }
         if (host_polled) check_host_kernel<<<1, 32, 0, s>>>(g->ctl, 1, order == CC_ORDER_11MM ? 1 : 2);
         else cc::check_kernel<<<1, 32, 0, s>>>(g->ctl, 1, loop, order == CC_ORDER_11MM ? 1 : 2);
+        return cudaGetLastError();
+    }
+    if (mode == CC_ASYNC_COMPACT) {
+        // one sweep per iteration: the compacting kernel or, once a compacting
+        // sweep was clean, the ordinary full-chain sweep over all edges
+        if constexpr (sizeof(IdT) == 4) {
+            int32_t* flag = &g->ctl->flag;
+            auto k = cc::mm_sweep_compact_kernel;
+            k<<<grid_for(k, g->m / 4 + 1), kThreads, 0, s>>>(static_cast<const int32_t*>(g->src),
+                                                            static_cast<const int32_t*>(g->dst), g->m, g->clists,
+                                                            (int32_t*)L, flag, g->ctl);
+            cudaError_t e = cudaGetLastError();
+            if (e != cudaSuccess) return e;
+            e = launch_sweep_t<0, false, IdT>(g, L, nullptr, cc::kFullChainHops, flag, 0, s, cc::kFullChainHops);
+            if (e != cudaSuccess) return e;
+        } else {
+            return cudaErrorInvalidValue;  // rejected by run_impl: int32 ids only
+        }
+        if (host_polled) cc::compact_check_host_kernel<<<1, 32, 0, s>>>(g->ctl);
+        else cc::compact_check_kernel<<<1, 32, 0, s>>>(g->ctl, loop);
         return cudaGetLastError();
     }
     for (int j = 0; j < c; ++j) {
@@ -648,10 +675,17 @@ static cc_status run_impl(cc_graph* g, int order, int mode, int c, int32_t max_s
         if (st != CC_OK) return st;
     }
     const bool schedule = order == CC_ORDER_11MM || order == CC_ORDER_1M1M;
-    if (schedule) c = 1;
+    if (schedule || mode == CC_ASYNC_COMPACT) c = 1;
     if ((order < 0 || order > CC_MAX_ORDER) && !schedule)
         return set_error(CC_EINVAL, "cc_run: order must be 1..%d, CC_ORDER_FULL, CC_ORDER_AUTO, CC_ORDER_11MM or CC_ORDER_1M1M", CC_MAX_ORDER);
-    if (mode != CC_SYNC && mode != CC_ASYNC) return set_error(CC_EINVAL, "cc_run: mode must be CC_SYNC or CC_ASYNC");
+    if (mode != CC_SYNC && mode != CC_ASYNC && mode != CC_ASYNC_COMPACT)
+        return set_error(CC_EINVAL, "cc_run: mode must be CC_SYNC, CC_ASYNC or CC_ASYNC_COMPACT");
+    if (mode == CC_ASYNC_COMPACT) {
+        if (order != CC_ORDER_FULL)
+            return set_error(CC_EINVAL, "cc_run: CC_ASYNC_COMPACT needs CC_ORDER_FULL (a finite order can split trees)");
+        if (g->id_bits != 32 || g->layout != CC_COO || g->hub_k > 0)
+            return set_error(CC_EINVAL, "cc_run: CC_ASYNC_COMPACT takes int32 edge lists (no native CSR, no hub layout)");
+    }
     if (c < 1 || c > 64) return set_error(CC_EINVAL, "cc_run: check_interval must be 1..64");
     if (max_sweeps < 1) return set_error(CC_EINVAL, "cc_run: max_sweeps must be >= 1");
     const size_t B = id_size(g->id_bits);
@@ -673,6 +707,17 @@ static cc_status run_impl(cc_graph* g, int order, int mode, int c, int32_t max_s
         if (!g->Lu) CC_CUDA(cc::dmalloc(&g->Lu, g->n * B, s));
         Lu = g->Lu;
     }
+    const bool compact = mode == CC_ASYNC_COMPACT;
+    if (compact && !g->clists.cnt) {
+        // two edge lists of the handle's size (a sweep keeps at most what it
+        // reads), then the counters; allocated before any loop graph captures them
+        const size_t bytes = (size_t)(g->m > 0 ? g->m : 1) * sizeof(int32_t);
+        for (int i = 0; i < 2; ++i) {
+            CC_CUDA(cc::dmalloc(reinterpret_cast<void**>(&g->clists.src[i]), bytes, s));
+            CC_CUDA(cc::dmalloc(reinterpret_cast<void**>(&g->clists.dst[i]), bytes, s));
+        }
+        CC_CUDA(cc::dmalloc(reinterpret_cast<void**>(&g->clists.cnt), 5 * sizeof(unsigned long long), s));
+    }
     cudaGraphExec_t loop = nullptr;
     const bool host_polled = g->launch == CC_LAUNCH_HOST;
     if (!host_polled) {
@@ -681,7 +726,8 @@ static cc_status run_impl(cc_graph* g, int order, int mode, int c, int32_t max_s
     }
 
     CC_CUDA(cudaEventRecord(g->ev0, s));
-    cc::ctl_reset_kernel<<<1, 32, 0, s>>>(g->ctl, max_sweeps, init_labels ? 0 : 1, schedule ? 1 : 0);
+    cc::ctl_reset_kernel<<<1, 32, 0, s>>>(g->ctl, max_sweeps, init_labels ? 0 : 1,
+                                          (schedule || mode == CC_ASYNC_COMPACT) ? 1 : 0);
     CC_LAUNCHED();
     CC_CUDA(g->id_bits == 64 ? enqueue_init<int64_t>(g, (int64_t*)L, (int64_t*)Lu, init_labels, s)
                              : enqueue_init<int32_t>(g, (int32_t*)L, (int32_t*)Lu, init_labels, s));
@@ -693,6 +739,7 @@ static cc_status run_impl(cc_graph* g, int order, int mode, int c, int32_t max_s
             return set_error(CC_EINVAL, "cc_run: init_labels violates 0 <= L[x] <= x at %llu entries (first %llu)",
                              g->ctl_h->bad_count, g->ctl_h->first_bad);
     }
+    if (compact) CC_CUDA(cudaMemsetAsync(g->clists.cnt, 0, 5 * sizeof(unsigned long long), s));
     CC_CUDA(cudaEventRecord(g->evl0, s));
     if (host_polled) {
         // one check block at a time; the host reads the control block after each
@@ -714,6 +761,8 @@ static cc_status run_impl(cc_graph* g, int order, int mode, int c, int32_t max_s
     if (L != labels_out)
         CC_CUDA(cudaMemcpyAsync(labels_out, L, g->n * B, cudaMemcpyDefault, s));
     CC_CUDA(cudaMemcpyAsync(g->ctl_h, g->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
+    unsigned long long cwords[2] = {0, 0};  // compacting runs: edges read and sweeps of the compacting phase
+    if (compact) CC_CUDA(cudaMemcpyAsync(cwords, g->clists.cnt + 3, sizeof cwords, cudaMemcpyDeviceToHost, s));
     CC_CUDA(cudaStreamSynchronize(s));
 
     const Ctl& h = *g->ctl_h;
@@ -731,7 +780,11 @@ static cc_status run_impl(cc_graph* g, int order, int mode, int c, int32_t max_s
                          ? B * (double)g->m + 8.0 * (double)(g->n + 1) + B * (double)g->n
                          : 2.0 * B * (double)g->m + B * (double)g->n;
         if (mode == CC_SYNC) per += 3.0 * B * (double)g->n;
-        stats->alg_bytes = per * h.sweeps;
+        // compacting runs: the compacting sweeps' edges (counted on the device)
+        // plus one full edge list for each ordinary sweep that followed
+        const double ordinary = (double)h.sweeps - (double)cwords[1];
+        stats->alg_bytes = compact ? 2.0 * B * ((double)cwords[0] + ordinary * (double)g->m) + B * (double)g->n * h.sweeps
+                                   : per * h.sweeps;
     }
     if (!h.converged)
         return set_error(CC_ENOTCONVERGED, "cc_run: not converged after %d sweeps", h.sweeps);
