@@ -50,6 +50,8 @@ def parse():
     p.add_argument("--cpu-seconds", type=float, default=12.0)
     p.add_argument("--batch-graphs", type=int, default=1024,
                    help="also compare batched + learned vs plain on a batch-mix of this many graphs (0: off)")
+    p.add_argument("--layout", choices=["coo", "csr", "csr-sym"], default="coo",
+                   help="main handle: edge list, or the same graph kept as CSR (each edge once / both directions)")
     p.add_argument("--launch", choices=["graph", "host"], default="graph",
                    help="sweep loop as a conditional CUDA graph, or host-polled blocks (for profilers)")
     p.add_argument("--reorder", choices=["none", "src", "lowdeg", "hub"], default="lowdeg",
@@ -308,9 +310,19 @@ def run_ours(args, rank, world, local):
     torch.cuda.empty_cache()  # release the generator's temporaries
     m = s.numel()
     stream = torch.cuda.current_stream()
-    g = cc.cc_init(n, s, d, stream=stream.cuda_stream)
+    if args.layout == "coo":
+        g = cc.cc_init(n, s, d, stream=stream.cuda_stream)
+    else:
+        sym = args.layout == "csr-sym"
+        off, cols = gg.to_csr(n, s, d, symmetric=sym)
+        g = cc.cc_init(n, off, cols, m=cols.numel(), id_bits=32, on_device=True, stream=stream.cuda_stream,
+                       layout=cc.CC_CSR_NATIVE_SYM if sym else cc.CC_CSR_NATIVE)
+        if args.reorder != "none":
+            raise SystemExit("--layout csr keeps the row order: use --reorder none")
     reorder = {"none": 0, "src": cc.CC_REORDER_SRC, "lowdeg": cc.CC_REORDER_LOWDEG,
                "hub": cc.CC_REORDER_HUB}[args.reorder]
+    if args.layout != "coo" and args.entry == "noalloc":
+        raise SystemExit("--entry noalloc takes edge lists: use --layout coo")
     if reorder == cc.CC_REORDER_HUB and args.entry == "noalloc":
         raise SystemExit("--entry noalloc takes plain edge lists; hub-encoded edges need cc_run")
     reorder_ms = None
@@ -341,11 +353,17 @@ def run_ours(args, rank, world, local):
     loop_ms = sum(st.loop_ms for st in stats) if edges is None else ms
     tot_sweeps = sum(sweeps)
     B = 4
-    per_sweep = 2 * B * m + B * n + (3 * B * n if mode == cc.CC_SYNC else 0)
+    if args.layout == "coo":
+        per_sweep = 2 * B * m + B * n + (3 * B * n if mode == cc.CC_SYNC else 0)
+        kernel = "mm_sweep_kernel"
+    else:  # native CSR: columns, offsets and labels once per sweep
+        nnz = m * (2 if args.layout == "csr-sym" else 1)
+        per_sweep = B * nnz + 8 * (n + 1) + B * n + (3 * B * n if mode == cc.CC_SYNC else 0)
+        kernel = "csr_sweep_kernel"
     sweep_ms = loop_ms / max(1, tot_sweeps)
     achieved = per_sweep / (sweep_ms * 1e-3) / 1e9
     peak, peak_kind = _peaks()
-    kname = f"mm_sweep_kernel<{args.order},{'sync' if mode == cc.CC_SYNC else 'async'},int32>"
+    kname = f"{kernel}<{args.order},{'sync' if mode == cc.CC_SYNC else 'async'},int32>"
     launches_per_run = [3 + sw * (2 if mode == cc.CC_SYNC else 1) + sw // args.interval for sw in sweeps]
 
     line = {
@@ -355,6 +373,8 @@ def run_ours(args, rank, world, local):
         "vs_baseline": None, "dtype": "int32", "data": "synthetic",
         "config": dict(cfg, n=n, m=m, order=args.order, mode=args.mode, check_interval=args.interval,
                        sweep_loop=("conditional CUDA graph" if args.launch == "graph" else "host-polled blocks"),
+                       layout={"coo": "edge list", "csr": "native CSR, each edge in its src row",
+                               "csr-sym": "native CSR, each edge in both rows"}[args.layout],
                        ids="int32", parallelism=f"replicas x{world}" if world > 1 else "single GPU",
                        l2="inputs larger than L2: edge list %.2f GB streamed every sweep" % (8 * m / 1e9),
                        edge_order=("as generated (shuffled)" if not reorder else
