@@ -49,13 +49,17 @@ typedef enum {
 
 enum { CC_ID32 = 32, CC_ID64 = 64 };
 enum { CC_COO = 0, CC_CSR = 1, CC_CSR_NATIVE = 2, CC_CSR_NATIVE_SYM = 3 };
-/* CC_ASYNC_COMPACT: asynchronous full-chain sweeps (order CC_ORDER_FULL only)
- * that drop every edge whose two chain walks ended at the same root: with the
- * full chain a tree never splits, so such an edge can never lower a label
- * again, and the final compress (every label set to the root of its chain)
- * gives its endpoints the same label.  Later sweeps read only the edges kept.
- * int32 edge lists only (no native CSR, no hub layout); the handle allocates
- * two more edge lists of its size on first use. */
+/* CC_ASYNC_COMPACT: asynchronous full-chain sweeps (order CC_ORDER_FULL only,
+ * check interval 1) that drop every edge whose two chain walks ended at the
+ * same root and pass the others to the next sweep, so later sweeps read only
+ * the edges that still merge trees.  Dropping is a heuristic (an asynchronous
+ * write that read a stale chain can still move a vertex to another tree), so
+ * convergence is decided as for CC_ASYNC (Section III-B2) over every edge:
+ * once a compacting sweep sees no violation, the next sweeps are ordinary
+ * full-chain sweeps over all edges until one sees none.  Labels are those of
+ * CC_ASYNC.  int32 edge lists only (no native CSR, no hub layout); the handle
+ * allocates two more edge lists of its size on first use.  No counterpart in
+ * the paper. */
 enum { CC_SYNC = 0, CC_ASYNC = 1, CC_ASYNC_COMPACT = 2 };
 /* Operator order: h >= 1 is MM^h of Def. 3; CC_ORDER_FULL follows each label
  * chain to its root (at most 1024 hops, the "C-m" variant with m = 1024 of
@@ -364,7 +368,8 @@ cc_status cc_graph_hubs(const cc_graph *g, const int32_t **hubs, int32_t *k);
  * at a time and reads the convergence flag after each; slower (a stream
  * synchronisation per block), but every kernel is an ordinary launch, for
  * profilers and debuggers that do not follow conditional graph nodes.  Both
- * give identical labels and sweep counts. */
+ * give identical labels and sweep counts.  (The paper's loop is a host
+ * do-while, Alg. 1; no counterpart for the graph form.) */
 enum { CC_LAUNCH_GRAPH = 0, CC_LAUNCH_HOST = 1 };
 cc_status cc_graph_set_launch(cc_graph *g, int launch);
 
