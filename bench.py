@@ -54,7 +54,7 @@ def parse():
                    help="main handle: edge list, or the same graph kept as CSR (each edge once / both directions)")
     p.add_argument("--launch", choices=["graph", "host"], default="graph",
                    help="sweep loop as a conditional CUDA graph, or host-polled blocks (for profilers)")
-    p.add_argument("--reorder", choices=["none", "src", "lowdeg", "hub"], default="lowdeg",
+    p.add_argument("--reorder", choices=["none", "src", "lowdeg", "hub"], default="hub",
                    help="cc_graph_reorder layout step once before timing (included in e2e)")
     p.add_argument("--entry", choices=["cc_run", "noalloc"], default="cc_run",
                    help="cc_run (conditional CUDA-graph loop) or cc_run_noalloc (host-polled "
@@ -251,15 +251,20 @@ def run_reference(args, rank, world):
 # our arm
 # ---------------------------------------------------------------------------
 
+def _source_sha(files):
+    h = hashlib.sha256()
+    for f in files:
+        h.update(open(os.path.join(ROOT, "paper_2311_02811_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()
+
+
 def _traffic_for(kernel: str):
-    """DRAM bytes per launch from the committed ncu summary, if it matches the source."""
+    """DRAM bytes per launch from the committed ncu summary, if it matches the
+    kernel's sources (the files listed in the entry, default mm_kernels.cuh)."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
-    src = os.path.join(ROOT, "paper_2311_02811_gb300", "csrc", "mm_kernels.cuh")
     try:
-        rec = json.load(open(path))
-        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
-        ent = rec.get(kernel)
-        if ent and ent.get("source_sha256") == sha:
+        ent = json.load(open(path)).get(kernel)
+        if ent and ent.get("source_sha256") == _source_sha(ent.get("sources", ["mm_kernels.cuh"])):
             return ent.get("dram_bytes_per_launch")
     except (OSError, ValueError):
         pass
@@ -355,7 +360,7 @@ def run_ours(args, rank, world, local):
     B = 4
     if args.layout == "coo":
         per_sweep = 2 * B * m + B * n + (3 * B * n if mode == cc.CC_SYNC else 0)
-        kernel = "mm_sweep_kernel"
+        kernel = "mm_sweep_hub_kernel" if cc.cc_graph_hubs(g)[1] > 0 else "mm_sweep_kernel"
     else:  # native CSR: columns, offsets and labels once per sweep
         nnz = m * (2 if args.layout == "csr-sym" else 1)
         per_sweep = B * nnz + 8 * (n + 1) + B * n + (3 * B * n if mode == cc.CC_SYNC else 0)
@@ -458,9 +463,16 @@ def variants(cc, g, out, n, m, args, dev, seed, stream, s=None, d=None):
     for order, mode, name in [(2, cc.CC_SYNC, "o2-sync"), (4, cc.CC_ASYNC, "o4-async"),
                               (4, cc.CC_SYNC, "o4-sync"), (0, cc.CC_ASYNC, "full-async"),
                               (1, cc.CC_ASYNC, "o1-async"), (cc.CC_ORDER_11MM, cc.CC_ASYNC, "c11mm-async"),
-                              (cc.CC_ORDER_1M1M, cc.CC_ASYNC, "c1m1m-async"),
-                              (0, cc.CC_ASYNC_COMPACT, "full-compact")]:
+                              (cc.CC_ORDER_1M1M, cc.CC_ASYNC, "c1m1m-async")]:
         res[f"{args.workload}/{name}"] = measure(g, out, n, m, order, mode, 1)
+    if s is not None:
+        # compaction takes plain edge lists: a lowdeg-reordered handle of the same graph
+        gl = cc.cc_init(n, s, d, stream=stream.cuda_stream)
+        cc.cc_graph_reorder(gl, cc.CC_REORDER_LOWDEG)
+        for order, mode, name in [(0, cc.CC_ASYNC, "full-async-lowdeg"), (0, cc.CC_ASYNC_COMPACT, "full-compact-lowdeg"),
+                                  (2, cc.CC_ASYNC, "o2-async-lowdeg")]:
+            res[f"{args.workload}/{name}"] = measure(gl, out, n, m, order, mode, 1)
+        cc.cc_free(gl)
     if os.path.exists(cc.SCHED_WEIGHTS_PATH):
         cc.load_default_scheduler()
         r = measure(g, out, n, m, cc.CC_ORDER_AUTO, cc.CC_ASYNC, 0)

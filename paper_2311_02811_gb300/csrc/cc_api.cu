@@ -262,10 +262,10 @@ static cudaError_t launch_sweep_t(const cc_graph* g, IdT* L, IdT* Lu, int h, int
     if constexpr (sizeof(IdT) == 4) {
         if (g->hub_k > 0) {
             auto kh = cc::mm_sweep_hub_kernel<H, SYNC>;
-            const size_t smem = (size_t)g->hub_k * 2 * sizeof(int32_t);
+            const size_t smem = (size_t)g->hub_k * sizeof(int32_t);
             // per device and cheap: set before every launch (or capture)
             cudaError_t e = cudaFuncSetAttribute(kh, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 cc::kHubMax * 2 * (int)sizeof(int32_t));
+                                                 cc::kHubMax * (int)sizeof(int32_t));
             if (e != cudaSuccess) return e;
             kh<<<cc::device_sms(), cc::kHubThreads, smem, s>>>(
                 static_cast<const int32_t*>(g->src), static_cast<const int32_t*>(g->dst), g->m, L, Lu, h, flag,

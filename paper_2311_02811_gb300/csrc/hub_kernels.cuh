@@ -9,6 +9,11 @@
 // half of the sweep's gathers: served from a shared-memory table, a warp's
 // 32 reads cost a few bank cycles instead of up to 32 L1 tag lookups.
 //
+// The table holds the hubs' labels only (4 bytes each, 96 KB at most), so
+// that most of the SM's L1 stays with the other gathers -- above all the
+// second-level ones, whose targets (roots) are few and hot.  A hub's id is
+// read from the global table (hubs) only when the sweep writes its label.
+//
 // The table is loaded from L at the start of every sweep.  Synchronous sweeps
 // never write L, so it is exact.  Asynchronous sweeps may read a table entry
 // that another block has lowered in L meanwhile; that is one more stale read
@@ -26,7 +31,7 @@
 namespace cc {
 
 constexpr int kHubThreads = 1024;   // one block per SM
-constexpr int kHubMax = 24576;      // table entries: 8 bytes each (label, id) -> 192 KB
+constexpr int kHubMax = 24576;      // table entries: one label each -> 96 KB
 constexpr int kHubMinDegree = 16;   // vertices of lower degree are not worth a slot
 
 // MM^h (h = H) on K edges whose v side may be a hub slot (see mm_fixed).
@@ -39,7 +44,7 @@ __device__ __forceinline__ bool mm_fixed_hub(const int32_t (&w)[K], const int32_
         cw[k][0] = w[k];
         cw[k][1] = rd<SYNC>(L, w[k]);
         if (venc[k] < 0) {
-            cv[k][0] = hubId[~venc[k]];
+            cv[k][0] = -1;  // id read from the global table only if written
             cv[k][1] = hubL[~venc[k]];
         } else {
             cv[k][0] = venc[k];
@@ -62,7 +67,7 @@ __device__ __forceinline__ bool mm_fixed_hub(const int32_t (&w)[K], const int32_
 #pragma unroll
         for (int j = 0; j < H; ++j) {
             if (cw[k][j + 1] > z) wr<SYNC>(L, Lu, cw[k][j], z);
-            if (cv[k][j + 1] > z) wr<SYNC>(L, Lu, cv[k][j], z);
+            if (cv[k][j + 1] > z) wr<SYNC>(L, Lu, (j == 0 && venc[k] < 0) ? hubId[~venc[k]] : cv[k][j], z);
         }
         if constexpr (!SYNC) {
             if (venc[k] < 0 && cv[k][1] > z) atomicMin(hubL + ~venc[k], z);
@@ -83,7 +88,7 @@ __device__ __forceinline__ bool mm_runtime_hub(const int32_t (&w)[K], const int3
         x[2 * k] = w[k];
         first[2 * k] = rd<SYNC>(L, w[k]);
         if (venc[k] < 0) {
-            x[2 * k + 1] = hubId[~venc[k]];
+            x[2 * k + 1] = -1;  // id read from the global table only if written
             first[2 * k + 1] = hubL[~venc[k]];
         } else {
             x[2 * k + 1] = venc[k];
@@ -112,6 +117,7 @@ __device__ __forceinline__ bool mm_runtime_hub(const int32_t (&w)[K], const int3
         z[k] = cur[2 * k] < cur[2 * k + 1] ? cur[2 * k] : cur[2 * k + 1];
         if (first[2 * k] > z[k]) wact |= 1u << (2 * k);
         if (first[2 * k + 1] > z[k]) {
+            if (venc[k] < 0) x[2 * k + 1] = hubId[~venc[k]];
             wact |= 1u << (2 * k + 1);
             if constexpr (!SYNC) {
                 if (venc[k] < 0) atomicMin(hubL + ~venc[k], z[k]);
@@ -140,7 +146,7 @@ __device__ __forceinline__ bool mm_runtime_hub(const int32_t (&w)[K], const int3
 }
 
 // The sweep (see mm_sweep_kernel for first / gate / flag).  One block of
-// kHubThreads per SM; dynamic shared memory: 8 * K bytes (labels, then ids).
+// kHubThreads per SM; dynamic shared memory: 4 * K bytes (the labels).
 template <int H, bool SYNC>
 __global__ void __launch_bounds__(kHubThreads, 1)
 mm_sweep_hub_kernel(const int32_t* __restrict__ src, const int32_t* __restrict__ dst, int64_t m, int32_t* L,
@@ -149,12 +155,8 @@ mm_sweep_hub_kernel(const int32_t* __restrict__ src, const int32_t* __restrict__
     if (gate != 0 && ctl->sched_h != gate) return;
     extern __shared__ int32_t hub_smem[];
     int32_t* hubL = hub_smem;
-    int32_t* hubId = hub_smem + K;
-    for (int i = threadIdx.x; i < K; i += blockDim.x) {
-        const int32_t v = hubs[i];
-        hubId[i] = v;
-        hubL[i] = rd<SYNC>(L, v);
-    }
+    const int32_t* hubId = hubs;  // ids stay in global memory
+    for (int i = threadIdx.x; i < K; i += blockDim.x) hubL[i] = rd<SYNC>(L, hubs[i]);
     __syncthreads();
     const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
