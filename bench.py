@@ -16,6 +16,7 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -48,7 +49,9 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
-    p.add_argument("--batch-graphs", type=int, default=1024,
+    p.add_argument("--no-config3", action="store_true",
+                   help="skip the R-MAT scale 27 and caterpillar lines of the default run")
+    p.add_argument("--batch-graphs", type=int, default=4096,
                    help="also compare batched + learned vs plain on a batch-mix of this many graphs (0: off)")
     p.add_argument("--layout", choices=["coo", "csr", "csr-sym"], default="coo",
                    help="main handle: edge list, or the same graph kept as CSR (each edge once / both directions)")
@@ -107,6 +110,46 @@ def max_over_ranks(x: float, world: int) -> float:
 # ---------------------------------------------------------------------------
 # workloads
 # ---------------------------------------------------------------------------
+
+def main_config(args, cfg, n, m):
+    """The workload description both arms print (identical for the same flags)."""
+    return dict(cfg, n=n, m=m, order=args.order, mode=args.mode, check_interval=args.interval,
+                layout={"coo": "edge list", "csr": "native CSR, each edge in its src row",
+                        "csr-sym": "native CSR, each edge in both rows"}[args.layout],
+                ids="int32", parallelism=f"replicas x{args.gpus}" if args.gpus > 1 else "single GPU",
+                l2="inputs larger than L2: edge list %.2f GB streamed every sweep" % (8 * m / 1e9))
+
+
+class OracleJob:
+    """The oracle's serial union-find on a background thread (the C call
+    releases the GIL), timed; its labels check the GPU labels of the same
+    graph."""
+
+    def __init__(self, n, s_host, d_host):
+        import threading
+
+        import oracle
+        oracle.build()
+        self.result = None
+        self.error = None
+
+        def run():
+            try:
+                t0 = time.perf_counter()
+                lab = oracle.uf_labels(n, s_host, d_host)
+                self.result = (lab, time.perf_counter() - t0)
+            except Exception as e:  # noqa: BLE001
+                self.error = repr(e)
+
+        self.thread = threading.Thread(target=run, daemon=True)
+        self.thread.start()
+
+    def get(self):
+        self.thread.join()
+        if self.error:
+            raise RuntimeError(f"oracle failed: {self.error}")
+        return self.result
+
 
 def make_workload(name: str, device, seed: int):
     if name.startswith("rmat"):
@@ -237,7 +280,7 @@ def run_reference(args, rank, world):
     tot_t = sum(dt for _, _, dt in rates)
     value = tot_edges / tot_t
     sample = f"serial union-find over the first {rates[-1][1]:,} of {m:,} edges (all {n:,} vertices) per step"
-    cfg.update(n=n, m=m, ids="int32")
+    cfg = main_config(args, cfg, n, m)
     line = {"impl": "reference", "metric": "CC edges/sec (m / solve time)", "value": value,
             "unit": "edges/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * tot_t / len(rates), "higher_is_better": True, "scaling": "weak",
@@ -315,6 +358,12 @@ def run_ours(args, rank, world, local):
     torch.cuda.empty_cache()  # release the generator's temporaries
     m = s.numel()
     stream = torch.cuda.current_stream()
+    cpu_leg = rank == 0 and world == 1 and not args.no_cpu
+    job = None
+    if cpu_leg:
+        # the oracle on the whole graph, on a host thread while the GPU works
+        s_h, d_h = s.cpu(), d.cpu()
+        job = OracleJob(n, s_h, d_h)
     if args.layout == "coo":
         g = cc.cc_init(n, s, d, stream=stream.cuda_stream)
     else:
@@ -353,6 +402,7 @@ def run_ours(args, rank, world, local):
     barrier(world)
     clocks = sampler.stop()
     value, ms_max = whole_job_rate(m * args.steps, ms, world)
+    timed_labels = out.cpu().numpy() if cpu_leg else None  # the last timed step's output
 
     sweeps = [st.sweeps for st in stats]
     loop_ms = sum(st.loop_ms for st in stats) if edges is None else ms
@@ -376,16 +426,13 @@ def run_ours(args, rank, world, local):
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-        "config": dict(cfg, n=n, m=m, order=args.order, mode=args.mode, check_interval=args.interval,
-                       sweep_loop=("conditional CUDA graph" if args.launch == "graph" else "host-polled blocks"),
-                       layout={"coo": "edge list", "csr": "native CSR, each edge in its src row",
-                               "csr-sym": "native CSR, each edge in both rows"}[args.layout],
-                       ids="int32", parallelism=f"replicas x{world}" if world > 1 else "single GPU",
-                       l2="inputs larger than L2: edge list %.2f GB streamed every sweep" % (8 * m / 1e9),
-                       edge_order=("as generated (shuffled)" if not reorder else
-                                   f"cc_graph_reorder({args.reorder}) once before timing, "
-                                   f"{reorder_ms:.1f} ms host-timed; inside the e2e timing"),
-                       sweeps_per_step=statistics.median(sweeps)),
+        "config": main_config(args, cfg, n, m),
+        "run": {"sweep_loop": ("conditional CUDA graph" if args.launch == "graph" else "host-polled blocks"),
+                "entry": args.entry,
+                "edge_order": ("as generated (shuffled)" if not reorder else
+                               f"cc_graph_reorder({args.reorder}) once before timing, "
+                               f"{reorder_ms:.1f} ms host-timed; inside the e2e timing"),
+                "sweeps_per_step": statistics.median(sweeps)},
         "roofline": {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak,
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": _traffic_for(kname),
@@ -403,17 +450,27 @@ def run_ours(args, rank, world, local):
 
     if not args.no_variants and rank == 0:
         line["variants"] = variants(cc, g, out, n, m, args, dev, seed, stream, s, d)
+    cc.cc_free(g)
+    del out
+    cc.cc_release_memory()  # the handles' pooled memory goes back before the larger graphs
+    if rank == 0 and world == 1 and not args.no_config3 and args.workload.startswith("rmat"):
+        del s, d
+        torch.cuda.empty_cache()
+        line["config3"] = config3(cc, args, dev, stream, with_oracle=cpu_leg)
+        cc.cc_release_memory()
+        torch.cuda.empty_cache()
     if args.batch_graphs > 0 and rank == 0:
         line["batch"] = batch_compare(cc, args.batch_graphs, args, dev, stream, gg.BASE_SEED + 3)
 
-    cc.cc_free(g)
-
-    if rank == 0 and world == 1 and not args.no_cpu:
-        s_h, d_h = s.cpu(), d.cpu()
-        rate, k, dt = cpu_oracle_rate(n, s_h, d_h, args.cpu_seconds)
-        line["cpu_baseline"] = {"value": rate, "unit": "edges/s", "cores": 1, "kind": "oracle",
-                                "sample": f"serial union-find over the first {k:,} of {m:,} edges "
-                                          f"(all {n:,} vertices), {dt:.1f} s"}
+    if "config3" in line:
+        finish_config3(line["config3"])
+    if cpu_leg:
+        want, dt = job.get()
+        line["labels_match_oracle"] = bool(np.array_equal(timed_labels, want))
+        line["cpu_baseline"] = {"value": m / dt, "unit": "edges/s", "cores": 1, "kind": "oracle",
+                                "sample": f"serial union-find over all {m:,} edges and {n:,} vertices "
+                                          f"of the timed graph, {dt:.1f} s; its labels are compared "
+                                          "with the last timed step's (labels_match_oracle)"}
         line["cpu_parallel"] = cpu_contour_rate(n, s_h, d_h, args.order if args.order > 0 else 1024)
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -451,14 +508,24 @@ def e2e(cc, n, s, d, args, mode, world, stream, reorder=0):
             "ms_per_step": ms / steps}
 
 
+def measure_solves(cc, gh, o, mm, order, mode, c, stream, reps=3):
+    """reps solves after one untimed one: edges/s, and the sweep loop's
+    algorithmic bytes over its CUDA-event time as a fraction of the peak."""
+    cc.cc_run(gh, o, order, mode, c)
+    ms, st = timed_runs(cc, gh, o, reps, order, mode, c, stream)
+    loop_ms = sum(x.loop_ms for x in st)
+    alg = sum(x.alg_bytes for x in st)
+    peak, _ = _peaks()
+    return {"edges_per_s": mm * reps / (ms * 1e-3), "ms": ms / reps, "sweeps": st[-1].sweeps,
+            "loop_ms": loop_ms / reps, "alg_bytes_per_solve": alg / reps,
+            "roofline_frac": alg / (loop_ms * 1e-3) / 1e9 / peak}
+
+
 def variants(cc, g, out, n, m, args, dev, seed, stream, s=None, d=None):
     res = {}
 
     def measure(gh, o, nn, mm, order, mode, c, reps=3):
-        cc.cc_run(gh, o, order, mode, c)
-        ms, st = timed_runs(cc, gh, o, reps, order, mode, c, stream)
-        return {"edges_per_s": mm * reps / (ms * 1e-3), "ms": ms / reps, "sweeps": st[-1].sweeps,
-                "loop_ms": st[-1].loop_ms}
+        return measure_solves(cc, gh, o, mm, order, mode, c, stream, reps)
 
     for order, mode, name in [(2, cc.CC_SYNC, "o2-sync"), (4, cc.CC_ASYNC, "o4-async"),
                               (4, cc.CC_SYNC, "o4-sync"), (0, cc.CC_ASYNC, "full-async"),
@@ -499,6 +566,11 @@ def variants(cc, g, out, n, m, args, dev, seed, stream, s=None, d=None):
     if args.workload.startswith("rmat"):
         n2, s2, d2, _ = make_workload("grid4096", dev, seed)
         g2 = cc.cc_init(n2, s2, d2, stream=stream.cuda_stream)
+        if args.reorder != "none":
+            # the same one-time layout step as the main handle (a grid has no
+            # vertex of degree >= 16, so the hub layout is the lowdeg one)
+            cc.cc_graph_reorder(g2, {"src": cc.CC_REORDER_SRC, "lowdeg": cc.CC_REORDER_LOWDEG,
+                                     "hub": cc.CC_REORDER_HUB}[args.reorder])
         o2 = torch.empty(n2, dtype=torch.int32, device=dev)
         for order, mode, name in [(2, cc.CC_ASYNC, "o2-async"), (2, cc.CC_SYNC, "o2-sync"),
                                   (4, cc.CC_ASYNC, "o4-async"), (0, cc.CC_ASYNC, "full-async"),
@@ -506,6 +578,81 @@ def variants(cc, g, out, n, m, args, dev, seed, stream, s=None, d=None):
             res[f"grid4096/{name}"] = measure(g2, o2, n2, s2.numel(), order, mode, 1)
         cc.cc_free(g2)
     return res
+
+
+def config3(cc, args, dev, stream, with_oracle):
+    """The two largest single graphs: R-MAT scale 27 (2^31 edges, so 64-bit
+    edge indices; labels 537 MB, larger than L2) and the caterpillar (2^24
+    backbone vertices with 15 leaves each: n = 2^28, diameter 2^24 + 1, the
+    d_max stress case of Lemma 2 and the Theorem).  Each is solved on the same
+    layout as the main handle.  R-MAT 27's labels are compared with the
+    oracle's union-find (run on a host thread; resolved by finish_config3);
+    the caterpillar is connected, so every label must be 0."""
+    reorder = {"none": 0, "src": cc.CC_REORDER_SRC, "lowdeg": cc.CC_REORDER_LOWDEG,
+               "hub": cc.CC_REORDER_HUB}[args.reorder]
+    res = {}
+    for name in ("rmat27", "caterpillar"):
+        t0 = time.perf_counter()
+        if name == "rmat27":
+            n = 1 << 27
+            s, d = gg.rmat(27, seed=gg.BASE_SEED, device=dev)
+            graph = "R-MAT a/b/c/d=.57/.19/.19/.05, scale 27, edge factor 16, ids permuted"
+        else:
+            B = 1 << 24
+            n = 16 * B
+            s, d = gg.caterpillar(B, seed=gg.BASE_SEED, device=dev)
+            graph = "caterpillar: 2^24-vertex path backbone + 15 leaves per backbone vertex, ids permuted"
+        torch.cuda.synchronize()
+        gen_s = time.perf_counter() - t0
+        torch.cuda.empty_cache()
+        m = s.numel()
+        job = OracleJob(n, s.cpu(), d.cpu()) if (with_oracle and name == "rmat27") else None
+        g = cc.cc_init(n, s, d, stream=stream.cuda_stream)
+        reorder_ms = None
+        if reorder:
+            t0 = time.perf_counter()
+            cc.cc_graph_reorder(g, reorder)
+            reorder_ms = 1e3 * (time.perf_counter() - t0)
+        del s, d  # the reordered handle owns its edges
+        torch.cuda.empty_cache()
+        out = torch.empty(n, dtype=torch.int32, device=dev)
+        ent = {"graph": graph, "n": n, "m": m, "edge_index_bits": 64 if m >= 1 << 31 else 32,
+               "generation_s": gen_s, "layout": args.reorder, "reorder_ms": reorder_ms,
+               "labels_bytes": 4 * n, "alg_bytes_per_async_sweep": 8 * m + 4 * n}
+        forms = {}
+        for order, mode, fname in [(2, cc.CC_ASYNC, "o2-async"), (0, cc.CC_ASYNC, "full-async"),
+                                   (2, cc.CC_SYNC, "o2-sync")]:
+            forms[fname] = measure_solves(cc, g, out, m, order, mode, 1, stream, reps=2)
+            if fname == "o2-async":
+                labels = out.cpu().numpy()
+        ent["forms"] = forms
+        if name == "caterpillar":
+            d_max = B + 1
+            bound = math.ceil(math.log(d_max) / math.log(1.5)) + 1
+            ent["theorem_bound_sync_o2"] = {"d_max": d_max, "bound": bound,
+                                            "sweeps_with_detection": forms["o2-sync"]["sweeps"],
+                                            "within_bound": forms["o2-sync"]["sweeps"] <= bound + 1}
+            ent["labels_match_closed_form"] = bool((labels == 0).all())
+        else:
+            ent["_pending"] = (job, labels) if job is not None else None
+        cc.cc_free(g)
+        del out, labels
+        torch.cuda.empty_cache()
+        res[name] = ent
+    return res
+
+
+def finish_config3(res):
+    """Join the oracle runs of config3() and record their checks."""
+    for ent in res.values():
+        pend = ent.pop("_pending", None)
+        if pend is None:
+            continue
+        job, labels = pend
+        want, dt = job.get()
+        ent["labels_match_oracle"] = bool(np.array_equal(labels, want))
+        ent["cpu_baseline"] = {"value": ent["m"] / dt, "unit": "edges/s", "cores": 1, "kind": "oracle",
+                               "sample": f"serial union-find over all {ent['m']:,} edges, {dt:.1f} s"}
 
 
 def make_batch(n_graphs: int, device, seed: int):

@@ -191,7 +191,9 @@ cc_status cc_run(cc_graph *g, int order, int mode, int check_interval, int32_t m
  *
  *   n, src, dst, m  int32 COO edges on the device (ids in [0, n), checked:
  *                   CC_EIDRANGE); src, dst and labels_out must be 16-byte
- *                   aligned (CC_EINVAL otherwise) and are never copied.
+ *                   aligned memory of the current device (device or managed
+ *                   allocations; host memory gives CC_EINVAL before any
+ *                   launch) and are never copied.
  *   order, mode, check_interval, max_sweeps  as for cc_run (no CC_ORDER_AUTO).
  *   labels_out      n int32 device labels; also the working label array.
  *   sweeps_out      NULL or the number of sweeps executed.
@@ -199,8 +201,10 @@ cc_status cc_run(cc_graph *g, int order, int mode, int check_interval, int32_t m
  *
  * Limits: CC_SYNC requires n <= CC_NOALLOC_MAX_N (CC_EINVAL beyond it, before
  * any device work); CC_ASYNC needs no L_u and accepts any n < 2^31.
- * The first call on each device looks up the array's device address (with
- * that device current), so make that first call before any stream capture.
+ * Every call looks up the array's address on the current device
+ * (cudaGetSymbolAddress, which allocates nothing); the first call on a device
+ * also loads the library's device code there, so make that first call before
+ * any stream capture.
  * Every call in the process shares the one array and clears the words it
  * needs at the start: calls that may overlap on the GPU (different streams or
  * threads) race and must be serialised by the caller.

@@ -181,11 +181,25 @@ def cc_run_noalloc(n, src, dst, labels_out, order=2, mode=CC_ASYNC, check_interv
 
     See cc_run_noalloc in contour.h: for callers that must not allocate device
     memory; scratch comes from a fixed array inside the library."""
-    ps, _ = _ptr(src)
-    pd, _ = _ptr(dst)
-    po, _ = _ptr(labels_out)
+    def dev_i32(x, what):
+        # a host array would reach the kernels as a host address, and an
+        # int64 tensor would be read as pairs of int32 ids: refuse both here
+        # (the library also refuses memory that is not on the current device)
+        if x is None or isinstance(x, int):
+            return x
+        if not hasattr(x, "data_ptr") or x.device.type != "cuda":
+            raise ValueError(f"cc_run_noalloc: {what} must be a CUDA tensor (or a device pointer)")
+        if str(x.dtype) != "torch.int32":
+            raise ValueError(f"cc_run_noalloc: {what} must be int32, got {x.dtype}")
+        if not x.is_contiguous():
+            raise ValueError(f"cc_run_noalloc: {what} must be contiguous")
+        return x.data_ptr()
+
+    ps = dev_i32(src, "src")
+    pd = dev_i32(dst, "dst")
+    po = dev_i32(labels_out, "labels_out")
     sw = _i32(0)
-    m = m if m is not None else (len(src) if src is not None else 0)
+    m = m if m is not None else (len(src) if src is not None and not isinstance(src, int) else 0)
     rc = lib.cc_run_noalloc(int(n), ps, pd, int(m), int(order),
                             int(mode), int(check_interval), int(max_sweeps), po,
                             ctypes.byref(sw), _stream(stream))

@@ -6,8 +6,6 @@
 // cudaFree, graph instantiation or other allocating call is made.
 #include <cuda_runtime.h>
 
-#include <mutex>
-
 #include "../../include/contour.h"
 #include "cc_internal.h"
 #include "mm_kernels.cuh"
@@ -24,25 +22,38 @@ static_assert(sizeof(Ctl) <= kCtlBytes, "control block does not fit its slot");
 // obtains the device address with cudaGetSymbolAddress (scratch_for_device).
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kCtlBytes + 4ull * CC_NOALLOC_MAX_N];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-void* g_scratch_ptr[kMaxDevices] = {};
-
-// Device address of the scratch array on the current device, looked up once
-// per device (with that device current).
+// Device address of the scratch array on the current device.  Looked up on
+// every call (cudaGetSymbolAddress allocates nothing): a cached address would
+// dangle after cudaDeviceReset or a new primary context reloads the module.
+// The first lookup on a device loads the library's device code there.
 cc_status scratch_for_device(unsigned char** out) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return cc::cuda_fail(e, "cudaGetSymbolAddress(g_noalloc_scratch)", __FILE__, __LINE__);
+    *out = static_cast<unsigned char*>(p);
+    return CC_OK;
+}
+
+// A kernel handed a host address faults (or, where the GPU can reach host
+// memory, silently works on the wrong memory): accept only memory of the
+// current device (device or managed allocations).  cudaPointerGetAttributes
+// allocates nothing.
+cc_status check_device_ptr(const void* p, const char* what) {
+    if (!p) return CC_OK;
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return cc::cuda_fail(e, "cudaGetDevice", __FILE__, __LINE__);
-    if (dev < 0 || dev >= kMaxDevices) return cc::set_error(CC_EINVAL, "cc_run_noalloc: device %d not supported", dev);
-    std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_scratch_ptr[dev]) {
-        void* p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess) return cc::cuda_fail(e, "cudaGetSymbolAddress(g_noalloc_scratch)", __FILE__, __LINE__);
-        g_scratch_ptr[dev] = p;
+    cudaPointerAttributes a = {};
+    e = cudaPointerGetAttributes(&a, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return cc::set_error(CC_EINVAL, "cc_run_noalloc: %s is not a CUDA pointer (%s)", what, cudaGetErrorString(e));
     }
-    *out = static_cast<unsigned char*>(g_scratch_ptr[dev]);
+    if (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged)
+        return cc::set_error(CC_EINVAL, "cc_run_noalloc: %s is not device memory", what);
+    if (a.type == cudaMemoryTypeDevice && a.device != dev)
+        return cc::set_error(CC_EINVAL, "cc_run_noalloc: %s lives on device %d, the current device is %d", what,
+                             a.device, dev);
     return CC_OK;
 }
 
@@ -110,8 +121,12 @@ extern "C" cc_status cc_run_noalloc(int64_t n, const int32_t* src, const int32_t
     if (sweeps_out) *sweeps_out = 0;
     if (n == 0) return CC_OK;
 
+    cc_status st = check_device_ptr(labels_out, "labels_out");
+    if (st == CC_OK && m > 0) st = check_device_ptr(src, "src");
+    if (st == CC_OK && m > 0) st = check_device_ptr(dst, "dst");
+    if (st != CC_OK) return st;
     unsigned char* scratch = nullptr;
-    cc_status st = scratch_for_device(&scratch);
+    st = scratch_for_device(&scratch);
     if (st != CC_OK) return st;
     Ctl* ctl = reinterpret_cast<Ctl*>(scratch);
     int32_t* Lu = (mode == CC_SYNC) ? reinterpret_cast<int32_t*>(scratch + kCtlBytes) : nullptr;

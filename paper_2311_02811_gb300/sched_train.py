@@ -163,7 +163,7 @@ def main():
     ap.add_argument("--chunk", type=int, default=500)
     ap.add_argument("--epochs", type=int, default=80)
     ap.add_argument("--out", default=os.path.join(HERE, "sched_weights.bin"))
-    ap.add_argument("--report", default=os.path.join(HERE, "sched_weights.json"))
+    ap.add_argument("--report", default=os.path.join(os.path.dirname(HERE), "profiles", "sched_weights.json"))
     ap.add_argument("--dump", default="", help="also save features, labels and timings (.npz)")
     ap.add_argument("--eval-only", action="store_true",
                     help="evaluate the weights in --out on the held-out set and update the report")

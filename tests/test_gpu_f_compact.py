@@ -113,9 +113,10 @@ def test_compact_full_size(cc, name):
     g = cc.cc_init(n, s, d)
     cc.cc_graph_reorder(g, cc.CC_REORDER_LOWDEG)
     out = torch.empty(n, dtype=torch.int32, device="cuda")
-    full = cc.cc_run(g, out, FULL, cc.CC_ASYNC, 1)
-    st = cc.cc_run(g, out, FULL, COMPACT, 1)
-    assert (out.cpu().numpy() == want).all()
-    if name == "rmat24":  # most edges drop after the first sweep of a power-law graph
-        assert st.alg_bytes < full.alg_bytes
+    # labels only: asynchronous sweep counts (and so the bytes a run moves)
+    # depend on thread timing; bench.py reports compaction's bytes and time
+    for mode in (cc.CC_ASYNC, COMPACT):
+        out.fill_(-1)
+        cc.cc_run(g, out, FULL, mode, 1)
+        assert (out.cpu().numpy() == want).all(), mode
     cc.cc_free(g)
