@@ -60,17 +60,34 @@ __device__ __forceinline__ bool mm_fixed_hub(const int32_t (&w)[K], const int32_
         }
     }
     bool viol = false;
+    int32_t z[K];
 #pragma unroll
     for (int k = 0; k < K; ++k) {
-        const int32_t z = cw[k][H] < cv[k][H] ? cw[k][H] : cv[k][H];
-        viol |= (cw[k][1] > z) | (cv[k][1] > z);
+        z[k] = cw[k][H] < cv[k][H] ? cw[k][H] : cv[k][H];
+        viol |= (cw[k][1] > z[k]) | (cv[k][1] > z[k]);
+    }
+    // w side: the edges are sorted by w, so a thread's edges often share w
+    // (and then their chains).  Equal chain vertices are adjacent; each run
+    // of them gets one write of the run's smallest z.  That equals the
+    // run's separate writes applied back to back: the conditional
+    // assignments of Def. 1 commute, and the smallest one wins.
 #pragma unroll
-        for (int j = 0; j < H; ++j) {
-            if (cw[k][j + 1] > z) wr<SYNC>(L, Lu, cw[k][j], z);
-            if (cv[k][j + 1] > z) wr<SYNC>(L, Lu, (j == 0 && venc[k] < 0) ? hubId[~venc[k]] : cv[k][j], z);
+    for (int j = 0; j < H; ++j) {
+        int32_t zr = z[0];
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            if (k > 0) zr = (cw[k][j] == cw[k - 1][j]) ? (zr < z[k] ? zr : z[k]) : z[k];
+            const bool last = (k == K - 1) || (cw[k + (k < K - 1)][j] != cw[k][j]);
+            if (last && cw[k][j + 1] > zr) wr<SYNC>(L, Lu, cw[k][j], zr);
         }
+    }
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+#pragma unroll
+        for (int j = 0; j < H; ++j)
+            if (cv[k][j + 1] > z[k]) wr<SYNC>(L, Lu, (j == 0 && venc[k] < 0) ? hubId[~venc[k]] : cv[k][j], z[k]);
         if constexpr (!SYNC) {
-            if (venc[k] < 0 && cv[k][1] > z) atomicMin(hubL + ~venc[k], z);
+            if (venc[k] < 0 && cv[k][1] > z[k]) atomicMin(hubL + ~venc[k], z[k]);
         }
     }
     return viol;
@@ -178,11 +195,26 @@ mm_sweep_hub_kernel(const int32_t* __restrict__ src, const int32_t* __restrict__
             viol |= identity_pair(__ldcs(src + t), v < 0 ? hubId[~v] : v, target);
         }
     } else {
+        // The next group's edges are loaded before this group's gathers, so
+        // the stream's DRAM latency overlaps the dependent label gathers.
         const int64_t q4 = m / 4;
+        int32_t wn[4], vn[4];
+        if (tid < q4) {
+            load4(src + tid * 4, wn);
+            load4(dst + tid * 4, vn);
+        }
         for (int64_t g = tid; g < q4; g += stride) {
             int32_t w[4], v[4];
-            load4(src + g * 4, w);
-            load4(dst + g * 4, v);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                w[k] = wn[k];
+                v[k] = vn[k];
+            }
+            const int64_t gn = g + stride;
+            if (gn < q4) {
+                load4(src + gn * 4, wn);
+                load4(dst + gn * 4, vn);
+            }
             if constexpr (H > 0) viol |= mm_fixed_hub<H, SYNC, 4>(w, v, L, Lu, hubL, hubId);
             else viol |= mm_runtime_hub<SYNC, 4>(w, v, h, L, Lu, hubL, hubId);
         }
