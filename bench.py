@@ -57,8 +57,10 @@ def parse():
                    help="main handle: edge list, or the same graph kept as CSR (each edge once / both directions)")
     p.add_argument("--launch", choices=["graph", "host"], default="graph",
                    help="sweep loop as a conditional CUDA graph, or host-polled blocks (for profilers)")
-    p.add_argument("--reorder", choices=["none", "src", "lowdeg", "hub"], default="hub",
+    p.add_argument("--reorder", choices=["none", "src", "lowdeg", "hub", "degree"], default="hub",
                    help="cc_graph_reorder layout step once before timing (included in e2e)")
+    p.add_argument("--config3-reorder", choices=["none", "lowdeg", "hub", "degree"], default="degree",
+                   help="layout of the R-MAT 27 and caterpillar handles")
     p.add_argument("--entry", choices=["cc_run", "noalloc"], default="cc_run",
                    help="cc_run (conditional CUDA-graph loop) or cc_run_noalloc (host-polled "
                         "plain launches of the same sweep kernel; profilers can see each sweep)")
@@ -110,6 +112,11 @@ def max_over_ranks(x: float, world: int) -> float:
 # ---------------------------------------------------------------------------
 # workloads
 # ---------------------------------------------------------------------------
+
+def REORDER(cc):
+    return {"none": 0, "src": cc.CC_REORDER_SRC, "lowdeg": cc.CC_REORDER_LOWDEG, "hub": cc.CC_REORDER_HUB,
+            "degree": cc.CC_REORDER_DEGREE}
+
 
 def main_config(args, cfg, n, m):
     """The workload description both arms print (identical for the same flags)."""
@@ -373,12 +380,11 @@ def run_ours(args, rank, world, local):
                        layout=cc.CC_CSR_NATIVE_SYM if sym else cc.CC_CSR_NATIVE)
         if args.reorder != "none":
             raise SystemExit("--layout csr keeps the row order: use --reorder none")
-    reorder = {"none": 0, "src": cc.CC_REORDER_SRC, "lowdeg": cc.CC_REORDER_LOWDEG,
-               "hub": cc.CC_REORDER_HUB}[args.reorder]
+    reorder = REORDER(cc)[args.reorder]
     if args.layout != "coo" and args.entry == "noalloc":
         raise SystemExit("--entry noalloc takes edge lists: use --layout coo")
-    if reorder == cc.CC_REORDER_HUB and args.entry == "noalloc":
-        raise SystemExit("--entry noalloc takes plain edge lists; hub-encoded edges need cc_run")
+    if reorder in (cc.CC_REORDER_HUB, cc.CC_REORDER_DEGREE) and args.entry == "noalloc":
+        raise SystemExit("--entry noalloc takes plain edge lists in the caller's ids; use --reorder none/src/lowdeg")
     reorder_ms = None
     if reorder:
         t0 = time.perf_counter()
@@ -540,6 +546,14 @@ def variants(cc, g, out, n, m, args, dev, seed, stream, s=None, d=None):
                                   (2, cc.CC_ASYNC, "o2-async-lowdeg")]:
             res[f"{args.workload}/{name}"] = measure(gl, out, n, m, order, mode, 1)
         cc.cc_free(gl)
+    if s is not None and args.reorder != "degree":
+        # the same graph renumbered by degree (labels mapped back to the caller's ids)
+        gd = cc.cc_init(n, s, d, stream=stream.cuda_stream)
+        cc.cc_graph_reorder(gd, cc.CC_REORDER_DEGREE)
+        for order, mode, name in [(2, cc.CC_SYNC, "o2-sync"), (2, cc.CC_ASYNC, "o2-async"),
+                                  (0, cc.CC_ASYNC, "full-async")]:
+            res[f"{args.workload}-degree/{name}"] = measure(gd, out, n, m, order, mode, 1)
+        cc.cc_free(gd)
     if os.path.exists(cc.SCHED_WEIGHTS_PATH):
         cc.load_default_scheduler()
         r = measure(g, out, n, m, cc.CC_ORDER_AUTO, cc.CC_ASYNC, 0)
@@ -569,8 +583,7 @@ def variants(cc, g, out, n, m, args, dev, seed, stream, s=None, d=None):
         if args.reorder != "none":
             # the same one-time layout step as the main handle (a grid has no
             # vertex of degree >= 16, so the hub layout is the lowdeg one)
-            cc.cc_graph_reorder(g2, {"src": cc.CC_REORDER_SRC, "lowdeg": cc.CC_REORDER_LOWDEG,
-                                     "hub": cc.CC_REORDER_HUB}[args.reorder])
+            cc.cc_graph_reorder(g2, REORDER(cc)[args.reorder])
         o2 = torch.empty(n2, dtype=torch.int32, device=dev)
         for order, mode, name in [(2, cc.CC_ASYNC, "o2-async"), (2, cc.CC_SYNC, "o2-sync"),
                                   (4, cc.CC_ASYNC, "o4-async"), (0, cc.CC_ASYNC, "full-async"),
@@ -588,8 +601,7 @@ def config3(cc, args, dev, stream, with_oracle):
     layout as the main handle.  R-MAT 27's labels are compared with the
     oracle's union-find (run on a host thread; resolved by finish_config3);
     the caterpillar is connected, so every label must be 0."""
-    reorder = {"none": 0, "src": cc.CC_REORDER_SRC, "lowdeg": cc.CC_REORDER_LOWDEG,
-               "hub": cc.CC_REORDER_HUB}[args.reorder]
+    reorder = REORDER(cc)[args.config3_reorder]
     res = {}
     for name in ("rmat27", "caterpillar"):
         t0 = time.perf_counter()
@@ -617,7 +629,7 @@ def config3(cc, args, dev, stream, with_oracle):
         torch.cuda.empty_cache()
         out = torch.empty(n, dtype=torch.int32, device=dev)
         ent = {"graph": graph, "n": n, "m": m, "edge_index_bits": 64 if m >= 1 << 31 else 32,
-               "generation_s": gen_s, "layout": args.reorder, "reorder_ms": reorder_ms,
+               "generation_s": gen_s, "layout": args.config3_reorder, "reorder_ms": reorder_ms,
                "labels_bytes": 4 * n, "alg_bytes_per_async_sweep": 8 * m + 4 * n}
         forms = {}
         for order, mode, fname in [(2, cc.CC_ASYNC, "o2-async"), (0, cc.CC_ASYNC, "full-async"),

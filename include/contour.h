@@ -356,15 +356,41 @@ cc_status cc_sched_train_step(const float *features_norm, const int32_t *labels,
  *                      for vertex hubs[~d] (cc_graph_hubs).  A graph without
  *                      such vertices keeps plain ids.  A hub-encoded handle
  *                      cannot be reordered again (CC_EINVAL).
+ *   CC_REORDER_DEGREE  renumber the vertices in order of decreasing degree
+ *                      (ties: smaller id first; vertex x becomes perm[x],
+ *                      cc_graph_perm), store every edge from its larger new
+ *                      id to its smaller and sort by the larger.  The labels
+ *                      of the first new ids (at most 24,576, each of degree
+ *                      >= 16) are read from a shared-memory copy.  The hot
+ *                      labels of a skewed graph then share
+ *                      few cache lines and stay in L2 even when the whole
+ *                      label array does not.  Sweeps run Alg. 1 / Section
+ *                      III-B on the renumbered graph; cc_run returns labels
+ *                      in the caller's ids, each tree of the final state
+ *                      labelled by its smallest caller id.  At convergence
+ *                      that is exactly the result of every other layout; a
+ *                      run stopped at max_sweeps returns a valid resume
+ *                      snapshot (not Alg. 1's state of the same sweep in the
+ *                      caller's ids), and init_labels are mapped in the same
+ *                      way.  The handle then holds two more n-entry id maps
+ *                      and two n-entry work arrays.  Renumbered handles take
+ *                      neither CC_ASYNC_COMPACT nor another reorder
+ *                      (CC_EINVAL).
  * CC_EINVAL for native CSR handles.
  */
-enum { CC_REORDER_SRC = 1, CC_REORDER_LOWDEG = 2, CC_REORDER_HUB = 3 };
+enum { CC_REORDER_SRC = 1, CC_REORDER_LOWDEG = 2, CC_REORDER_HUB = 3, CC_REORDER_DEGREE = 4 };
 cc_status cc_graph_reorder(cc_graph *g, int method);
 
 /* The hub table of a CC_REORDER_HUB handle: *hubs (device, *k int32 ids) is
- * NULL and *k is 0 when the edges carry no hub entries.  Valid until cc_free
- * or the next cc_graph_reorder. */
+ * NULL and *k is 0 when the edges carry no hub entries.  For a
+ * CC_REORDER_DEGREE handle *hubs is NULL and *k is the number of new ids read
+ * from shared memory.  Valid until cc_free or the next cc_graph_reorder. */
 cc_status cc_graph_hubs(const cc_graph *g, const int32_t **hubs, int32_t *k);
+
+/* The id maps of a CC_REORDER_DEGREE handle (device, n int32 each): perm[x]
+ * is the new id of vertex x, inv the inverse.  Both NULL for other handles.
+ * Valid until cc_free. */
+cc_status cc_graph_perm(const cc_graph *g, const int32_t **perm, const int32_t **inv);
 
 /* How cc_run drives the sweep loop.  CC_LAUNCH_GRAPH (default): one CUDA
  * graph whose conditional WHILE node repeats the check blocks on the device,
@@ -388,7 +414,8 @@ cc_status cc_graph_info(const cc_graph *g, int64_t *n, int64_t *m);
  * handle's own copy after cc_init copied or cc_graph_reorder reordered it);
  * valid until cc_free or the next cc_graph_reorder.  For the native CSR
  * layouts *src receives the int64 offsets and *dst the columns; after
- * CC_REORDER_HUB the dst array holds hub entries ~s (see cc_graph_hubs). */
+ * CC_REORDER_HUB the dst array holds hub entries ~s (see cc_graph_hubs), and
+ * after CC_REORDER_DEGREE both arrays hold new ids (see cc_graph_perm). */
 cc_status cc_graph_edges(const cc_graph *g, const void **src, const void **dst);
 
 /* Release a handle and every device buffer it owns.  NULL is ignored.  The

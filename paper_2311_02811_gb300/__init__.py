@@ -23,7 +23,7 @@ __all__ = [
     "cc_batch_run", "cc_batch_set_schedule", "cc_batch_run_scheduled", "cc_batch_tuning",
     "cc_batch_set_tuning", "cc_batch_reorder", "cc_batch_edges", "cc_batch_free", "cc_batch", "cc_sched_load", "cc_sched_blob_bytes",
     "cc_sched_param_count", "cc_sched_decode", "cc_graph_features", "cc_batch_features",
-    "cc_sched_predict", "cc_sched_train", "load_default_scheduler", "SCHED_WEIGHTS_PATH", "cc_sched_train_step", "CC_SCHED_FEATURES", "CC_SCHED_CLASSES", "cc_graph_info", "cc_graph_edges", "cc_graph_set_stream", "cc_graph_reorder", "CC_REORDER_SRC", "CC_REORDER_LOWDEG", "CC_REORDER_HUB", "cc_graph_hubs", "cc_graph_set_launch", "CC_LAUNCH_GRAPH", "CC_LAUNCH_HOST", "cc_strerror",
+    "cc_sched_predict", "cc_sched_train", "load_default_scheduler", "SCHED_WEIGHTS_PATH", "cc_sched_train_step", "CC_SCHED_FEATURES", "CC_SCHED_CLASSES", "cc_graph_info", "cc_graph_edges", "cc_graph_set_stream", "cc_graph_reorder", "CC_REORDER_SRC", "CC_REORDER_LOWDEG", "CC_REORDER_HUB", "CC_REORDER_DEGREE", "cc_graph_hubs", "cc_graph_perm", "cc_graph_set_launch", "CC_LAUNCH_GRAPH", "CC_LAUNCH_HOST", "cc_strerror",
     "cc_last_error",
 ]
 
@@ -453,7 +453,7 @@ def cc_sched_train_step(features_std, labels, params, lr):
     return p, loss.value
 
 
-CC_REORDER_SRC, CC_REORDER_LOWDEG, CC_REORDER_HUB = 1, 2, 3
+CC_REORDER_SRC, CC_REORDER_LOWDEG, CC_REORDER_HUB, CC_REORDER_DEGREE = 1, 2, 3, 4
 lib.cc_graph_reorder.argtypes = [_p, _int]
 lib.cc_graph_reorder.restype = _int
 
@@ -485,6 +485,18 @@ def cc_graph_hubs(g):
     a, k = _p(), _i32(0)
     _check(lib.cc_graph_hubs(g, ctypes.byref(a), ctypes.byref(k)), "cc_graph_hubs")
     return a.value, k.value
+
+
+lib.cc_graph_perm.argtypes = [_p, ctypes.POINTER(_p), ctypes.POINTER(_p)]
+lib.cc_graph_perm.restype = _int
+
+
+def cc_graph_perm(g):
+    """(perm, inv) device pointers (ints) of a CC_REORDER_DEGREE handle's id maps
+    (perm[x] = new id of vertex x); (None, None) for other handles."""
+    a, b = _p(), _p()
+    _check(lib.cc_graph_perm(g, ctypes.byref(a), ctypes.byref(b)), "cc_graph_perm")
+    return a.value, b.value
 
 
 CC_LAUNCH_GRAPH, CC_LAUNCH_HOST = 0, 1

@@ -25,6 +25,7 @@
 #include "csr_kernels.cuh"
 #include "hub_kernels.cuh"
 #include "compact_kernels.cuh"
+#include "relabel_kernels.cuh"
 
 using cc::Ctl;
 
@@ -181,7 +182,11 @@ struct cc_graph {
     bool own_off = false;
     int32_t* seg = nullptr;   // native CSR: row of every 4th entry
     int32_t* hubs = nullptr;  // CC_REORDER_HUB: dst entry ~s names hubs[s]
-    int hub_k = 0;
+    int hub_k = 0;            // hub table entries (CC_REORDER_DEGREE: new ids read from shared memory)
+    int32_t* perm = nullptr;  // CC_REORDER_DEGREE: new id of every vertex
+    int32_t* inv = nullptr;   //   and its inverse
+    int32_t* tree_min = nullptr;  //   work arrays of the label mapping
+    int32_t* Lx = nullptr;
     int launch = CC_LAUNCH_GRAPH;  // or CC_LAUNCH_HOST (cc_graph_set_launch)
     cc::CompactLists clists = {};  // CC_ASYNC_COMPACT: two edge lists + counters (allocated on first use)
     void* L = nullptr;   // working labels when the caller's output is on the host
@@ -216,6 +221,10 @@ static void destroy(cc_graph* g) {
     if (g->own_off) cc::dfree(g->off, g->stream);
     cc::dfree(g->seg, g->stream);
     cc::dfree(g->hubs, g->stream);
+    cc::dfree(g->perm, g->stream);
+    cc::dfree(g->inv, g->stream);
+    cc::dfree(g->tree_min, g->stream);
+    cc::dfree(g->Lx, g->stream);
     for (int i = 0; i < 2; ++i) {
         cc::dfree(g->clists.src[i], g->stream);
         cc::dfree(g->clists.dst[i], g->stream);
@@ -260,6 +269,19 @@ static cudaError_t launch_sweep_t(const cc_graph* g, IdT* L, IdT* Lu, int h, int
         }
     }
     if constexpr (sizeof(IdT) == 4) {
+        if (g->perm) {
+            auto kp = cc::mm_sweep_prefix_kernel<H, SYNC>;
+            // synchronous sweeps hold two tables (labels and L_u minima) in the same space
+            const int kt = SYNC ? (g->hub_k < cc::kHubMax / 2 ? g->hub_k : cc::kHubMax / 2) : g->hub_k;
+            const size_t smem = (size_t)kt * (SYNC ? 2 : 1) * sizeof(int32_t);
+            cudaError_t e = cudaFuncSetAttribute(kp, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 cc::kHubMax * (int)sizeof(int32_t));
+            if (e != cudaSuccess) return e;
+            kp<<<cc::device_sms(), cc::kHubThreads, smem, s>>>(static_cast<const int32_t*>(g->src),
+                                                                static_cast<const int32_t*>(g->dst), g->m, L, Lu,
+                                                                h, flag, g->ctl, first, gate, kt);
+            return cudaGetLastError();
+        }
         if (g->hub_k > 0) {
             auto kh = cc::mm_sweep_hub_kernel<H, SYNC>;
             const size_t smem = (size_t)g->hub_k * sizeof(int32_t);
@@ -639,6 +661,23 @@ static cudaError_t enqueue_init(cc_graph* g, IdT* L, IdT* Lu, const void* init, 
     return cudaGetLastError();
 }
 
+// Label mapping of a renumbered handle (relabel_kernels.cuh): every tree of
+// src gets the smallest key[] of its members, and out[x] = that minimum for
+// the tree of map[x].  Export: src = the new-id labels, key = inv, map = perm.
+// Import: src = a snapshot in the caller's ids, key = perm, map = inv.
+static cudaError_t enqueue_map(cc_graph* g, const int32_t* src, const int32_t* key, const int32_t* map,
+                               int32_t* out, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(g->tree_min, 0x7f, (size_t)g->n * sizeof(int32_t), s);  // > every id
+    if (e != cudaSuccess) return e;
+    auto kt = cc::tree_min_kernel;
+    kt<<<grid_for(kt, g->n / 64 + 1), kThreads, 0, s>>>(src, key, g->n, g->tree_min, 0, &g->ctl->bad_count);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    auto km = cc::map_labels_kernel;
+    km<<<grid_for(km, g->n), kThreads, 0, s>>>(src, map, g->tree_min, g->n, out, 0, &g->ctl->bad_count);
+    return cudaGetLastError();
+}
+
 template <typename IdT>
 static cudaError_t enqueue_compress(cc_graph* g, IdT* L, cudaStream_t s) {
     auto k = cc::compress_kernel<IdT>;
@@ -683,8 +722,9 @@ static cc_status run_impl(cc_graph* g, int order, int mode, int c, int32_t max_s
     if (mode == CC_ASYNC_COMPACT) {
         if (order != CC_ORDER_FULL)
             return set_error(CC_EINVAL, "cc_run: CC_ASYNC_COMPACT needs CC_ORDER_FULL (a finite order can split trees)");
-        if (g->id_bits != 32 || g->layout != CC_COO || g->hub_k > 0)
-            return set_error(CC_EINVAL, "cc_run: CC_ASYNC_COMPACT takes int32 edge lists (no native CSR, no hub layout)");
+        if (g->id_bits != 32 || g->layout != CC_COO || g->hub_k > 0 || g->perm)
+            return set_error(CC_EINVAL, "cc_run: CC_ASYNC_COMPACT takes int32 edge lists (no native CSR, no hub or "
+                                        "renumbered layout)");
     }
     if (c < 1 || c > 64) return set_error(CC_EINVAL, "cc_run: check_interval must be 1..64");
     if (max_sweeps < 1) return set_error(CC_EINVAL, "cc_run: max_sweeps must be >= 1");
@@ -698,9 +738,14 @@ static cc_status run_impl(cc_graph* g, int order, int mode, int c, int32_t max_s
     if (g->n == 0) return CC_OK;
 
     void* L = labels_out;
-    if (!out_on_device || (reinterpret_cast<uintptr_t>(labels_out) & 15)) {
+    const bool relabeled = g->perm != nullptr;  // sweeps work on the renumbered ids
+    if (relabeled || !out_on_device || (reinterpret_cast<uintptr_t>(labels_out) & 15)) {
         if (!g->L) CC_CUDA(cc::dmalloc(&g->L, g->n * B, s));
         L = g->L;
+    }
+    if (relabeled) {
+        if (!g->tree_min) CC_CUDA(cc::dmalloc(reinterpret_cast<void**>(&g->tree_min), g->n * sizeof(int32_t), s));
+        if (!g->Lx) CC_CUDA(cc::dmalloc(reinterpret_cast<void**>(&g->Lx), g->n * sizeof(int32_t), s));
     }
     void* Lu = nullptr;
     if (mode == CC_SYNC) {
@@ -729,8 +774,16 @@ static cc_status run_impl(cc_graph* g, int order, int mode, int c, int32_t max_s
     cc::ctl_reset_kernel<<<1, 32, 0, s>>>(g->ctl, max_sweeps, init_labels ? 0 : 1,
                                           (schedule || mode == CC_ASYNC_COMPACT) ? 1 : 0);
     CC_LAUNCHED();
-    CC_CUDA(g->id_bits == 64 ? enqueue_init<int64_t>(g, (int64_t*)L, (int64_t*)Lu, init_labels, s)
-                             : enqueue_init<int32_t>(g, (int32_t*)L, (int32_t*)Lu, init_labels, s));
+    if (relabeled && init_labels) {
+        // a snapshot in the caller's ids: validated here, mapped below
+        CC_CUDA(cudaMemcpyAsync(g->Lx, init_labels, g->n * sizeof(int32_t), cudaMemcpyDefault, s));
+        auto kv = cc::validate_snapshot_kernel<int32_t>;
+        kv<<<grid_for(kv, g->n), kThreads, 0, s>>>(g->Lx, g->n, g->ctl);
+        CC_LAUNCHED();
+    } else {
+        CC_CUDA(g->id_bits == 64 ? enqueue_init<int64_t>(g, (int64_t*)L, (int64_t*)Lu, init_labels, s)
+                                 : enqueue_init<int32_t>(g, (int32_t*)L, (int32_t*)Lu, init_labels, s));
+    }
     if (init_labels) {
         // a bad snapshot could point outside [0, n): check before any gather
         CC_CUDA(cudaMemcpyAsync(g->ctl_h, g->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
@@ -738,6 +791,11 @@ static cc_status run_impl(cc_graph* g, int order, int mode, int c, int32_t max_s
         if (g->ctl_h->bad_count)
             return set_error(CC_EINVAL, "cc_run: init_labels violates 0 <= L[x] <= x at %llu entries (first %llu)",
                              g->ctl_h->bad_count, g->ctl_h->first_bad);
+    }
+    if (relabeled && init_labels) {
+        // each tree of the snapshot gets its smallest new id
+        CC_CUDA(enqueue_map(g, g->Lx, g->perm, g->inv, (int32_t*)L, s));
+        if (Lu) CC_CUDA(launch_copy<int32_t>((int32_t*)Lu, (const int32_t*)L, g->n, s));
     }
     if (compact) CC_CUDA(cudaMemsetAsync(g->clists.cnt, 0, 5 * sizeof(unsigned long long), s));
     CC_CUDA(cudaEventRecord(g->evl0, s));
@@ -757,9 +815,16 @@ static cc_status run_impl(cc_graph* g, int order, int mode, int c, int32_t max_s
     CC_CUDA(cudaEventRecord(g->evl1, s));
     CC_CUDA(g->id_bits == 64 ? enqueue_compress<int64_t>(g, (int64_t*)L, s)
                              : enqueue_compress<int32_t>(g, (int32_t*)L, s));
+    void* result = L;
+    if (relabeled) {
+        // back to the caller's ids: each tree labelled by its smallest member
+        const bool direct = out_on_device && (reinterpret_cast<uintptr_t>(labels_out) & 3) == 0;
+        result = direct ? labels_out : g->Lx;
+        CC_CUDA(enqueue_map(g, (const int32_t*)L, g->inv, g->perm, (int32_t*)result, s));
+    }
     CC_CUDA(cudaEventRecord(g->ev1, s));
-    if (L != labels_out)
-        CC_CUDA(cudaMemcpyAsync(labels_out, L, g->n * B, cudaMemcpyDefault, s));
+    if (result != labels_out)
+        CC_CUDA(cudaMemcpyAsync(labels_out, result, g->n * B, cudaMemcpyDefault, s));
     CC_CUDA(cudaMemcpyAsync(g->ctl_h, g->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
     unsigned long long cwords[2] = {0, 0};  // compacting runs: edges read and sweeps of the compacting phase
     if (compact) CC_CUDA(cudaMemcpyAsync(cwords, g->clists.cnt + 3, sizeof cwords, cudaMemcpyDeviceToHost, s));
@@ -786,6 +851,8 @@ static cc_status run_impl(cc_graph* g, int order, int mode, int c, int32_t max_s
         stats->alg_bytes = compact ? 2.0 * B * ((double)cwords[0] + ordinary * (double)g->m) + B * (double)g->n * h.sweeps
                                    : per * h.sweeps;
     }
+    if (relabeled && h.bad_count)
+        return set_error(CC_ECUDA, "cc_run: label chain longer than %d hops while mapping ids", cc::kMapChaseCap);
     if (!h.converged)
         return set_error(CC_ENOTCONVERGED, "cc_run: not converged after %d sweeps", h.sweeps);
     if (h.compress_changes)
@@ -818,6 +885,13 @@ extern "C" cc_status cc_graph_hubs(const cc_graph* g, const int32_t** hubs, int3
     if (!g) return set_error(CC_EINVAL, "cc_graph_hubs: g is NULL");
     if (hubs) *hubs = g->hubs;
     if (k) *k = g->hub_k;
+    return CC_OK;
+}
+
+extern "C" cc_status cc_graph_perm(const cc_graph* g, const int32_t** perm, const int32_t** inv) {
+    if (!g) return set_error(CC_EINVAL, "cc_graph_perm: g is NULL");
+    if (perm) *perm = g->perm;
+    if (inv) *inv = g->inv;
     return CC_OK;
 }
 
@@ -862,6 +936,15 @@ void graph_set_hubs(cc_graph* g, int32_t* hubs, int k) {
 const int64_t* graph_csr_off(const cc_graph* g) { return g->off; }
 cudaStream_t graph_stream(const cc_graph* g) { return g->stream; }
 SchedCtx** graph_sched_slot(cc_graph* g) { return &g->sched; }
+void graph_set_relabel(cc_graph* g, int32_t* perm, int32_t* inv, int k) {
+    free_loops(g);  // loop graphs captured the previous sweep kernel
+    dfree(g->perm, g->stream);
+    dfree(g->inv, g->stream);
+    g->perm = perm;
+    g->inv = inv;
+    g->hub_k = k;
+}
+bool graph_relabeled(const cc_graph* g) { return g->perm != nullptr; }
 cc_status graph_replace_edges(cc_graph* g, void* src, void* dst) {
     // cached loop graphs and scheduler features refer to the old arrays
     free_loops(g);

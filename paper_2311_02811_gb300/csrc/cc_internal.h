@@ -42,6 +42,10 @@ cudaStream_t graph_stream(const cc_graph* g);
 SchedCtx** graph_sched_slot(cc_graph* g);
 // Replace the handle's edge arrays by device arrays it then owns (reorder.cu).
 cc_status graph_replace_edges(cc_graph* g, void* src, void* dst);
+// CC_REORDER_DEGREE: hand the id maps (n int32 each, owned by the handle from
+// then on) and the shared-memory prefix length to the handle.
+void graph_set_relabel(cc_graph* g, int32_t* perm, int32_t* inv, int k);
+bool graph_relabeled(const cc_graph* g);
 
 // CC_ORDER_AUTO: pick (order, mode, check interval) for a graph; the plain
 // order-2 synchronous schedule with c = 1 when no scheduler weights are loaded.

@@ -18,6 +18,13 @@
 //                      kHubMinDegree, become hubs: a dst entry naming hub
 //                      number s is stored as ~s, and the sweep reads the hubs'
 //                      labels from a shared-memory table (hub_kernels.cuh)
+//   CC_REORDER_DEGREE  renumber the vertices in order of decreasing degree
+//                      (ties: smaller id first), store every edge from its
+//                      larger new id to its smaller and sort by the larger;
+//                      the first (at most kHubMax) new ids of degree at least
+//                      kHubMinDegree are read from shared memory at every
+//                      step of a chain (relabel_kernels.cuh).  cc_run maps
+//                      the labels back to the caller's ids.
 #include <cub/device/device_radix_sort.cuh>
 #include <cuda_runtime.h>
 
@@ -27,6 +34,7 @@
 #include "../../include/contour.h"
 #include "cc_internal.h"
 #include "hub_kernels.cuh"
+#include "relabel_kernels.cuh"
 
 namespace {
 
@@ -152,25 +160,114 @@ done:
     return st;
 }
 
+// CC_REORDER_DEGREE: renumber, orient, sort; hands the new edges, the two
+// id maps and the shared-memory prefix length to the handle.
+cc_status relabel_by_degree(cc_graph* g, const int32_t* src, const int32_t* dst, int64_t n, int64_t m,
+                            cudaStream_t s) {
+    cc_status st = CC_OK;
+    int32_t *deg = nullptr, *deg_sorted = nullptr, *perm = nullptr;
+    uint32_t *ids = nullptr, *inv = nullptr, *k_in = nullptr, *v_in = nullptr, *k_out = nullptr, *v_out = nullptr;
+    void* tmp = nullptr;
+    size_t tmp_bytes = 0, need = 0;
+    const int grid = cc::device_sms() * 8;
+    const int cap = (int)std::min<int64_t>(n, cc::kHubMax);
+    std::vector<int32_t> top(cap > 0 ? cap : 1);
+    int K = 0;
+    RCUDA(cc::dmalloc(reinterpret_cast<void**>(&deg), (size_t)n * sizeof(int32_t), s));
+    RCUDA(cc::dmalloc(reinterpret_cast<void**>(&deg_sorted), (size_t)n * sizeof(int32_t), s));
+    RCUDA(cc::dmalloc(reinterpret_cast<void**>(&ids), (size_t)n * sizeof(uint32_t), s));
+    RCUDA(cc::dmalloc(reinterpret_cast<void**>(&inv), (size_t)n * sizeof(uint32_t), s));
+    RCUDA(cc::dmalloc(reinterpret_cast<void**>(&perm), (size_t)n * sizeof(int32_t), s));
+    RCUDA(cudaMemsetAsync(deg, 0, (size_t)n * sizeof(int32_t), s));
+    degree_kernel<<<grid, 256, 0, s>>>(src, dst, m, deg);
+    RCUDA(cudaGetLastError());
+    iota_u32_kernel<<<grid, 256, 0, s>>>(ids, n);
+    RCUDA(cudaGetLastError());
+    // stable: equal degrees keep increasing ids
+    RCUDA(cub::DeviceRadixSort::SortPairsDescending(nullptr, need, deg, deg_sorted, ids, inv, (long long)n, 0, 32, s));
+    tmp_bytes = need;
+    RCUDA(cub::DeviceRadixSort::SortPairs(nullptr, need, k_in, k_out, v_in, v_out, (long long)m, 0, bits_for(n), s));
+    tmp_bytes = std::max(tmp_bytes, need);
+    RCUDA(cc::dmalloc(&tmp, tmp_bytes, s));
+    RCUDA(cub::DeviceRadixSort::SortPairsDescending(tmp, tmp_bytes, deg, deg_sorted, ids, inv, (long long)n, 0, 32, s));
+    if (cap > 0) RCUDA(cudaMemcpyAsync(top.data(), deg_sorted, (size_t)cap * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    cc::invert_perm_kernel<<<grid, 256, 0, s>>>(inv, n, perm);
+    RCUDA(cudaGetLastError());
+    cc::dfree(deg, s);
+    cc::dfree(deg_sorted, s);
+    cc::dfree(ids, s);
+    deg = deg_sorted = nullptr;
+    ids = nullptr;
+    RCUDA(cc::dmalloc(reinterpret_cast<void**>(&k_in), (size_t)m * sizeof(uint32_t), s));
+    RCUDA(cc::dmalloc(reinterpret_cast<void**>(&v_in), (size_t)m * sizeof(uint32_t), s));
+    RCUDA(cc::dmalloc(reinterpret_cast<void**>(&k_out), (size_t)m * sizeof(uint32_t), s));
+    RCUDA(cc::dmalloc(reinterpret_cast<void**>(&v_out), (size_t)m * sizeof(uint32_t), s));
+    cc::relabel_orient_kernel<<<grid, 256, 0, s>>>(src, dst, m, perm, k_in, v_in);
+    RCUDA(cudaGetLastError());
+    RCUDA(cub::DeviceRadixSort::SortPairs(tmp, tmp_bytes, k_in, k_out, v_in, v_out, (long long)m, 0, bits_for(n), s));
+    RCUDA(cudaStreamSynchronize(s));
+    while (K < cap && top[K] >= cc::kHubMinDegree) ++K;
+    {
+        // every stored id must be in range before the handle gathers with it
+        unsigned long long* d_bad = nullptr;
+        unsigned long long bad = 0;
+        RCUDA(cc::dmalloc(reinterpret_cast<void**>(&d_bad), sizeof bad, s));
+        RCUDA(cudaMemsetAsync(d_bad, 0, sizeof bad, s));
+        range_check_kernel<<<grid, 256, 0, s>>>(k_out, v_out, m, n, 0, d_bad);
+        cudaError_t e2 = cudaGetLastError();
+        if (e2 == cudaSuccess) e2 = cudaMemcpyAsync(&bad, d_bad, sizeof bad, cudaMemcpyDeviceToHost, s);
+        if (e2 == cudaSuccess) e2 = cudaStreamSynchronize(s);
+        cc::dfree(d_bad, s);
+        RCUDA(e2);
+        if (bad) {
+            st = cc::set_error(CC_ECUDA, "cc_graph_reorder: internal error, %llu renumbered ids out of range", bad);
+            goto done;
+        }
+    }
+    st = cc::graph_replace_edges(g, k_out, v_out);
+    if (st == CC_OK) {
+        k_out = v_out = nullptr;  // now owned by the handle
+        cc::graph_set_relabel(g, perm, reinterpret_cast<int32_t*>(inv), K);
+        perm = nullptr;
+        inv = nullptr;
+    }
+done:
+    cc::dfree(deg, s);
+    cc::dfree(deg_sorted, s);
+    cc::dfree(ids, s);
+    cc::dfree(inv, s);
+    cc::dfree(perm, s);
+    cc::dfree(k_in, s);
+    cc::dfree(v_in, s);
+    cc::dfree(k_out, s);
+    cc::dfree(v_out, s);
+    cc::dfree(tmp, s);
+    return st;
+}
+
 }  // namespace
 
 extern "C" cc_status cc_graph_reorder(cc_graph* g, int method) {
     cc::NvtxRange range("cc_graph_reorder");
     if (!g) return cc::set_error(CC_EINVAL, "cc_graph_reorder: g is NULL");
-    if (method != CC_REORDER_SRC && method != CC_REORDER_LOWDEG && method != CC_REORDER_HUB)
-        return cc::set_error(CC_EINVAL,
-                             "cc_graph_reorder: method must be CC_REORDER_SRC, CC_REORDER_LOWDEG or CC_REORDER_HUB");
+    if (method != CC_REORDER_SRC && method != CC_REORDER_LOWDEG && method != CC_REORDER_HUB &&
+        method != CC_REORDER_DEGREE)
+        return cc::set_error(CC_EINVAL, "cc_graph_reorder: method must be CC_REORDER_SRC, CC_REORDER_LOWDEG, "
+                                        "CC_REORDER_HUB or CC_REORDER_DEGREE");
     if (cc::graph_id_bits(g) != 32) return cc::set_error(CC_EINVAL, "cc_graph_reorder: int32 ids only");
     if (cc::graph_layout(g) != CC_COO)
         return cc::set_error(CC_EINVAL, "cc_graph_reorder: a native CSR handle keeps the caller's row order");
     if (cc::graph_hub_count(g) > 0)
         return cc::set_error(CC_EINVAL, "cc_graph_reorder: the edges are already hub-encoded (CC_REORDER_HUB)");
+    if (cc::graph_relabeled(g))
+        return cc::set_error(CC_EINVAL, "cc_graph_reorder: the vertices are already renumbered (CC_REORDER_DEGREE)");
     long long n = 0, m = 0;
     cc::graph_nm(g, &n, &m);
     if (m == 0) return CC_OK;
     cudaStream_t s = cc::graph_stream(g);
     const int32_t* src = static_cast<const int32_t*>(cc::graph_src(g));
     const int32_t* dst = static_cast<const int32_t*>(cc::graph_dst(g));
+    if (method == CC_REORDER_DEGREE) return relabel_by_degree(g, src, dst, n, m, s);
     cc_status st = CC_OK;
     uint32_t *k_in = nullptr, *v_in = nullptr, *k_out = nullptr, *v_out = nullptr;
     int32_t* deg = nullptr;

@@ -806,7 +806,7 @@ static cc_status handle_features(cc_graph* g, cudaStream_t s) {
     cc::graph_nm(g, &n, &m);
     cc::SchedCtx** slot = cc::graph_sched_slot(g);
     const int layout = cc::graph_layout(g);
-    if (layout == CC_COO && cc::graph_hub_count(g) > 0) {  // hub-encoded edges: decode a sample
+    if (layout == CC_COO && cc::graph_hubs(g) != nullptr) {  // hub-encoded edges: decode a sample
         const long long S = m < kSample ? m : kSample;
         const int64_t ov[2] = {0, n}, oe[2] = {0, S};
         cc_status st = ctx_get(slot, 1, ov, oe, s);

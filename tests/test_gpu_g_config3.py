@@ -50,6 +50,21 @@ def test_caterpillar_2pow24_backbone(cc):
     bound = math.ceil(math.log(diameter) / math.log(1.5)) + 1
     assert st.sweeps <= bound + 1, (st.sweeps, bound)
     cc.cc_free(g)
+    del out
+    # renumbered by degree: the backbone takes the first 2^24 ids; the
+    # Theorem's bound holds for the renumbered graph as well (same diameter)
+    s, d = gg.caterpillar(B, device="cuda")
+    g = cc.cc_init(n, s, d)
+    cc.cc_graph_reorder(g, cc.CC_REORDER_DEGREE)
+    del s, d
+    torch.cuda.empty_cache()
+    for order, mode in [(2, cc.CC_ASYNC), (0, cc.CC_ASYNC), (2, cc.CC_SYNC)]:
+        out, st = _solve(cc, g, n, order, mode)
+        assert int(out.max()) == 0 and int(out.min()) == 0, (order, mode)
+        if mode == cc.CC_SYNC:
+            assert st.sweeps <= bound + 1, (st.sweeps, bound)
+        del out
+    cc.cc_free(g)
 
 
 def test_rmat_scale27_int64_edge_offsets(cc):
@@ -67,6 +82,16 @@ def test_rmat_scale27_int64_edge_offsets(cc):
     assert torch.equal(out, out_r)
     cc.cc_free(g)
     del out_r
+    # renumbered by degree (the layout the bench times at this size): every
+    # form maps back to the same labels
+    torch.cuda.empty_cache()
+    g = cc.cc_init(n, s, d)
+    cc.cc_graph_reorder(g, cc.CC_REORDER_DEGREE)
+    for order, mode in [(2, cc.CC_ASYNC), (0, cc.CC_ASYNC), (2, cc.CC_SYNC)]:
+        out_d, _ = _solve(cc, g, n, order, mode)
+        assert torch.equal(out, out_d), (order, mode)
+        del out_d
+    cc.cc_free(g)
     del out, out_full
     want = oracle.uf_labels(n, s.cpu().numpy(), d.cpu().numpy())
     assert np.array_equal(got, want)
