@@ -41,7 +41,7 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--workload", default="rmat24",
-                   help="rmat<scale> (default rmat24), grid4096, components64, batch<G> or delaunay-scaling")
+                   help="rmat<scale> (default rmat24), grid4096, caterpillar, components64, batch<G> or delaunay-scaling")
     p.add_argument("--order", type=int, default=2)
     p.add_argument("--mode", choices=["async", "sync"], default="async")
     p.add_argument("--interval", type=int, default=1)
@@ -164,6 +164,10 @@ def make_workload(name: str, device, seed: int):
         s, d = gg.rmat(scale, seed=seed, device=device)
         return (1 << scale), s, d, {"workload": f"rmat-scale{scale}",
                                     "graph": "R-MAT a/b/c/d=.57/.19/.19/.05, edge factor 16, ids permuted"}
+    if name == "caterpillar":
+        s, d = gg.caterpillar(1 << 24, seed=seed, device=device)
+        return 1 << 28, s, d, {"workload": "caterpillar-2^24",
+                               "graph": "2^24-vertex path backbone + 15 leaves per backbone vertex, ids permuted"}
     if name == "grid4096":
         s, d = gg.grid(4096, 4096, seed=seed, device=device)
         return 4096 * 4096, s, d, {"workload": "grid-4096x4096", "graph": "4-neighbour grid, 5% edges deleted, ids permuted"}
@@ -308,12 +312,13 @@ def _source_sha(files):
     return h.hexdigest()
 
 
-def _traffic_for(kernel: str):
-    """DRAM bytes per launch from the committed ncu summary, if it matches the
-    kernel's sources (the files listed in the entry, default mm_kernels.cuh)."""
+def _traffic_for(kernel: str, workload: str):
+    """DRAM bytes per launch from the committed ncu summary of this kernel on
+    this workload, if it matches the kernel's sources (the files listed in the
+    entry, default mm_kernels.cuh)."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
-        ent = json.load(open(path)).get(kernel)
+        ent = json.load(open(path)).get(f"{kernel}@{workload}")
         if ent and ent.get("source_sha256") == _source_sha(ent.get("sources", ["mm_kernels.cuh"])):
             return ent.get("dram_bytes_per_launch")
     except (OSError, ValueError):
@@ -416,7 +421,8 @@ def run_ours(args, rank, world, local):
     B = 4
     if args.layout == "coo":
         per_sweep = 2 * B * m + B * n + (3 * B * n if mode == cc.CC_SYNC else 0)
-        kernel = "mm_sweep_hub_kernel" if cc.cc_graph_hubs(g)[1] > 0 else "mm_sweep_kernel"
+        kernel = ("mm_sweep_prefix_kernel" if cc.cc_graph_perm(g)[0] else
+                  "mm_sweep_hub_kernel" if cc.cc_graph_hubs(g)[1] > 0 else "mm_sweep_kernel")
     else:  # native CSR: columns, offsets and labels once per sweep
         nnz = m * (2 if args.layout == "csr-sym" else 1)
         per_sweep = B * nnz + 8 * (n + 1) + B * n + (3 * B * n if mode == cc.CC_SYNC else 0)
@@ -441,7 +447,7 @@ def run_ours(args, rank, world, local):
                 "sweeps_per_step": statistics.median(sweeps)},
         "roofline": {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak,
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": _traffic_for(kname),
+                     "traffic": _traffic_for(kname, cfg["workload"]),
                      "alg_bytes_per_launch": per_sweep,
                      "launch_ms": sweep_ms,
                      "timing": "sweep-loop CUDA events on the launching stream / sweeps (includes the per-block check kernel)"},

@@ -663,18 +663,21 @@ static cudaError_t enqueue_init(cc_graph* g, IdT* L, IdT* Lu, const void* init, 
 
 // Label mapping of a renumbered handle (relabel_kernels.cuh): every tree of
 // src gets the smallest key[] of its members, and out[x] = that minimum for
-// the tree of map[x].  Export: src = the new-id labels, key = inv, map = perm.
-// Import: src = a snapshot in the caller's ids, key = perm, map = inv.
+// the tree of map[x].  Export: src = the new-id labels, key = inv, map = perm;
+// stars_if_converged: after a converged loop and its compress the trees are
+// stars (read from the control block on the device).  Import: src = a
+// snapshot in the caller's ids, key = perm, map = inv, chains walked.
 static cudaError_t enqueue_map(cc_graph* g, const int32_t* src, const int32_t* key, const int32_t* map,
-                               int32_t* out, cudaStream_t s) {
+                               int32_t* out, cudaStream_t s, bool stars_if_converged) {
+    const Ctl* ctl = stars_if_converged ? g->ctl : nullptr;
     cudaError_t e = cudaMemsetAsync(g->tree_min, 0x7f, (size_t)g->n * sizeof(int32_t), s);  // > every id
     if (e != cudaSuccess) return e;
     auto kt = cc::tree_min_kernel;
-    kt<<<grid_for(kt, g->n / 64 + 1), kThreads, 0, s>>>(src, key, g->n, g->tree_min, 0, &g->ctl->bad_count);
+    kt<<<grid_for(kt, g->n / 64 + 1), kThreads, 0, s>>>(src, key, g->n, g->tree_min, ctl, &g->ctl->bad_count);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     auto km = cc::map_labels_kernel;
-    km<<<grid_for(km, g->n), kThreads, 0, s>>>(src, map, g->tree_min, g->n, out, 0, &g->ctl->bad_count);
+    km<<<grid_for(km, g->n), kThreads, 0, s>>>(src, map, g->tree_min, g->n, out, ctl, &g->ctl->bad_count);
     return cudaGetLastError();
 }
 
@@ -794,7 +797,7 @@ static cc_status run_impl(cc_graph* g, int order, int mode, int c, int32_t max_s
     }
     if (relabeled && init_labels) {
         // each tree of the snapshot gets its smallest new id
-        CC_CUDA(enqueue_map(g, g->Lx, g->perm, g->inv, (int32_t*)L, s));
+        CC_CUDA(enqueue_map(g, g->Lx, g->perm, g->inv, (int32_t*)L, s, false));
         if (Lu) CC_CUDA(launch_copy<int32_t>((int32_t*)Lu, (const int32_t*)L, g->n, s));
     }
     if (compact) CC_CUDA(cudaMemsetAsync(g->clists.cnt, 0, 5 * sizeof(unsigned long long), s));
@@ -820,7 +823,7 @@ static cc_status run_impl(cc_graph* g, int order, int mode, int c, int32_t max_s
         // back to the caller's ids: each tree labelled by its smallest member
         const bool direct = out_on_device && (reinterpret_cast<uintptr_t>(labels_out) & 3) == 0;
         result = direct ? labels_out : g->Lx;
-        CC_CUDA(enqueue_map(g, (const int32_t*)L, g->inv, g->perm, (int32_t*)result, s));
+        CC_CUDA(enqueue_map(g, (const int32_t*)L, g->inv, g->perm, (int32_t*)result, s, true));
     }
     CC_CUDA(cudaEventRecord(g->ev1, s));
     if (result != labels_out)

@@ -66,6 +66,9 @@ __device__ __forceinline__ bool mm_fixed_hub(const int32_t (&w)[K], const int32_
         z[k] = cw[k][H] < cv[k][H] ? cw[k][H] : cv[k][H];
         viol |= (cw[k][1] > z[k]) | (cv[k][1] > z[k]);
     }
+    // chains never increase, so no write is due unless some first label
+    // exceeds z: the common case of a late sweep skips the write logic
+    if (!viol) return false;
     // w side: the edges are sorted by w, so a thread's edges often share w
     // (and then their chains).  Equal chain vertices are adjacent; each run
     // of them gets one write of the run's smallest z.  That equals the

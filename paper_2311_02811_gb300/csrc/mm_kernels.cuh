@@ -112,17 +112,22 @@ __device__ __forceinline__ bool mm_fixed(const IdT (&w)[K], const IdT (&v)[K], I
         }
     }
     bool viol = false;
+    IdT z[K];
 #pragma unroll
     for (int k = 0; k < K; ++k) {
-        const IdT z = cw[k][H] < cv[k][H] ? cw[k][H] : cv[k][H];
-        viol |= (cw[k][1] > z) | (cv[k][1] > z);
+        z[k] = cw[k][H] < cv[k][H] ? cw[k][H] : cv[k][H];
+        viol |= (cw[k][1] > z[k]) | (cv[k][1] > z[k]);
+    }
+    if (!viol) return false;  // the common case of a late sweep: no write is due
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
 #pragma unroll
         for (int j = 0; j < H; ++j) {
-            if (cw[k][j + 1] > z) wr<SYNC>(L, Lu, cw[k][j], z);
-            if (cv[k][j + 1] > z) wr<SYNC>(L, Lu, cv[k][j], z);
+            if (cw[k][j + 1] > z[k]) wr<SYNC>(L, Lu, cw[k][j], z[k]);
+            if (cv[k][j + 1] > z[k]) wr<SYNC>(L, Lu, cv[k][j], z[k]);
         }
     }
-    return viol;
+    return true;
 }
 
 // ---------------------------------------------------------------------------

@@ -94,6 +94,7 @@ __device__ __forceinline__ bool mm_fixed_prefix(const int32_t (&w)[K], const int
         z[k] = cw[k][H] < cv[k][H] ? cw[k][H] : cv[k][H];
         viol |= (cw[k][1] > z[k]) | (cv[k][1] > z[k]);
     }
+    if (!viol) return false;  // no write is due (see mm_fixed_hub)
 #pragma unroll
     for (int j = 0; j < H; ++j) {
         int32_t zr = z[0];
@@ -202,15 +203,19 @@ mm_sweep_prefix_kernel(const int32_t* __restrict__ src, const int32_t* __restric
     const int64_t q4 = m / 4;
     if (ident) {
         // from L = id every chain is trivial: the larger endpoint (stored
-        // first) takes the smaller id (see mm_sweep_kernel)
+        // first) takes the smaller id (see mm_sweep_kernel); one write per run
+        // of equal w with the run's smallest v (a loop has v == w: no write)
         for (int64_t g = tid; g < q4; g += stride) {
             int32_t w[4], v[4];
             load4(src + g * 4, w);
             load4(dst + g * 4, v);
+            int32_t zr = v[0];
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
-                if (w[k] != v[k]) {
-                    pwr<SYNC>(L, Lu, tab, KH, w[k], v[k]);
+                if (k > 0) zr = (w[k] == w[k - 1]) ? (zr < v[k] ? zr : v[k]) : v[k];
+                const bool last = (k == 3) || (w[k + (k < 3)] != w[k]);
+                if (last && zr < w[k]) {
+                    pwr<SYNC>(L, Lu, tab, KH, w[k], zr);
                     viol = true;
                 }
             }
@@ -281,28 +286,46 @@ __device__ __forceinline__ int32_t chase_root(const int32_t* L, int32_t x, unsig
 // share one root (the giant component's), so each lane keeps a running
 // minimum per run of equal roots over its slice of a warp tile and issues one
 // atomic per run; a warp whose lanes all end on the same root issues one.
-// stars != 0: L is a set of stars (after the compress), root(y) = L[y].
+// ctl != nullptr and ctl->converged: the compress has made L a set of stars,
+// root(y) = L[y], and a lane's loads are independent (4 in flight per step);
+// otherwise every chain is walked to its root.
 static __global__ void tree_min_kernel(const int32_t* L, const int32_t* key, int64_t n, int32_t* tree_min,
-                                       int stars, unsigned long long* overflow) {
+                                       const Ctl* ctl, unsigned long long* overflow) {
     constexpr int kPerLane = 64;
+    const bool stars = ctl != nullptr && ctl->converged != 0;
     const int lane = threadIdx.x & 31;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const int64_t tile = 32 * kPerLane;
     int32_t racc = -1, kacc = 0x7fffffff;
+    auto take = [&](int32_t r, int32_t kv) {
+        if (r == racc) {
+            kacc = kv < kacc ? kv : kacc;
+        } else {
+            if (racc >= 0) atomicMin(tree_min + racc, kacc);
+            racc = r;
+            kacc = kv;
+        }
+    };
     for (int64_t base = warp * tile; base < n; base += nwarps * tile) {
+        if (stars && base + tile <= n) {
+            for (int i = 0; i < kPerLane; i += 4) {
+                int32_t r[4], kv[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int64_t y = base + (int64_t)(i + u) * 32 + lane;
+                    r[u] = L[y];
+                    kv[u] = key[y];
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) take(r[u], kv[u]);
+            }
+            continue;
+        }
         for (int i = 0; i < kPerLane; ++i) {
             const int64_t y = base + (int64_t)i * 32 + lane;
             if (y >= n) break;
-            const int32_t r = stars ? L[y] : chase_root(L, (int32_t)y, overflow);
-            const int32_t kv = key[y];
-            if (r == racc) {
-                kacc = kv < kacc ? kv : kacc;
-            } else {
-                if (racc >= 0) atomicMin(tree_min + racc, kacc);
-                racc = r;
-                kacc = kv;
-            }
+            take(stars ? L[y] : chase_root(L, (int32_t)y, overflow), key[y]);
         }
     }
     const int32_t r0 = __shfl_sync(0xffffffffu, racc, 0);
@@ -318,9 +341,11 @@ static __global__ void tree_min_kernel(const int32_t* L, const int32_t* key, int
 }
 
 // out[x] = tree_min[root(map[x])]: labels of one id space from a label array
-// of the other (map: caller id -> renumbered id, or the reverse).
+// of the other (map: caller id -> renumbered id, or the reverse); stars as
+// for tree_min_kernel.
 static __global__ void map_labels_kernel(const int32_t* L, const int32_t* map, const int32_t* tree_min, int64_t n,
-                                         int32_t* out, int stars, unsigned long long* overflow) {
+                                         int32_t* out, const Ctl* ctl, unsigned long long* overflow) {
+    const bool stars = ctl != nullptr && ctl->converged != 0;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += stride) {
         const int32_t y = map[x];
