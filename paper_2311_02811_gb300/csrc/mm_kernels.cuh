@@ -119,13 +119,26 @@ __device__ __forceinline__ bool mm_fixed(const IdT (&w)[K], const IdT (&v)[K], I
         viol |= (cw[k][1] > z[k]) | (cv[k][1] > z[k]);
     }
     if (!viol) return false;  // the common case of a late sweep: no write is due
+    // w side: after cc_graph_reorder the edges are sorted by w, so a thread's
+    // edges often share w (and then their chains).  Equal chain vertices are
+    // adjacent; each run of them gets one write of the run's smallest z, which
+    // equals the run's separate writes applied back to back (the conditional
+    // assignments of Def. 1 commute, and the smallest wins).
+#pragma unroll
+    for (int j = 0; j < H; ++j) {
+        IdT zr = z[0];
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            if (k > 0) zr = (cw[k][j] == cw[k - 1][j]) ? (zr < z[k] ? zr : z[k]) : z[k];
+            const bool last = (k == K - 1) || (cw[k + (k < K - 1)][j] != cw[k][j]);
+            if (last && cw[k][j + 1] > zr) wr<SYNC>(L, Lu, cw[k][j], zr);
+        }
+    }
 #pragma unroll
     for (int k = 0; k < K; ++k) {
 #pragma unroll
-        for (int j = 0; j < H; ++j) {
-            if (cw[k][j + 1] > z[k]) wr<SYNC>(L, Lu, cw[k][j], z[k]);
+        for (int j = 0; j < H; ++j)
             if (cv[k][j + 1] > z[k]) wr<SYNC>(L, Lu, cv[k][j], z[k]);
-        }
     }
     return true;
 }
@@ -267,8 +280,10 @@ __device__ __forceinline__ bool identity_pair(IdT w, IdT v, IdT* target) {
     return true;
 }
 
+// Four resident blocks (64 registers) for int32 ids, 4 edges per thread and
+// h <= 2; two for the wider cases, which would spill under that cap.
 template <int H, bool SYNC, int G, typename IdT>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, (sizeof(IdT) == 4 && G == 1 && H <= 2 && H > 0) ? 4 : 2)
 mm_sweep_kernel(const IdT* __restrict__ src, const IdT* __restrict__ dst, int64_t m,
                 IdT* L, IdT* Lu, int h, int32_t* flag, const Ctl* ctl, int first, int gate) {
     if (gate != 0 && ctl->sched_h != gate) return;
@@ -294,18 +309,30 @@ mm_sweep_kernel(const IdT* __restrict__ src, const IdT* __restrict__ dst, int64_
         }
         return;
     }
-    for (int64_t g = tid; g < ngroups; g += stride) {
-        IdT w[4 * G], v[4 * G];
+    // The next group's edges are loaded before this group's gathers, so the
+    // stream's DRAM latency overlaps the dependent label gathers.
+    IdT wn[4 * G], vn[4 * G];
+    auto load_group = [&](int64_t gg) {
 #pragma unroll
         for (int q = 0; q < G; ++q) {
             IdT t[4];
-            load4(src + (g * G + q) * 4, t);
+            load4(src + (gg * G + q) * 4, t);
 #pragma unroll
-            for (int i = 0; i < 4; ++i) w[4 * q + i] = t[i];
-            load4(dst + (g * G + q) * 4, t);
+            for (int i = 0; i < 4; ++i) wn[4 * q + i] = t[i];
+            load4(dst + (gg * G + q) * 4, t);
 #pragma unroll
-            for (int i = 0; i < 4; ++i) v[4 * q + i] = t[i];
+            for (int i = 0; i < 4; ++i) vn[4 * q + i] = t[i];
         }
+    };
+    if (tid < ngroups) load_group(tid);
+    for (int64_t g = tid; g < ngroups; g += stride) {
+        IdT w[4 * G], v[4 * G];
+#pragma unroll
+        for (int i = 0; i < 4 * G; ++i) {
+            w[i] = wn[i];
+            v[i] = vn[i];
+        }
+        if (g + stride < ngroups) load_group(g + stride);
         if constexpr (H > 0) {
             viol |= mm_fixed<H, SYNC, 4 * G>(w, v, L, Lu);
         } else {
