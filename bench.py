@@ -644,6 +644,13 @@ def config3(cc, args, dev, stream, with_oracle):
             if fname == "o2-async":
                 labels = out.cpu().numpy()
         ent["forms"] = forms
+        kern = {"degree": "mm_sweep_prefix_kernel", "hub": "mm_sweep_hub_kernel"}.get(args.config3_reorder,
+                                                                                     "mm_sweep_kernel")
+        wl = "rmat-scale27" if name == "rmat27" else "caterpillar-2^24"
+        forms["o2-async"]["kernel"] = f"{kern}<2,async,int32>"
+        forms["o2-async"]["traffic_per_sweep"] = _traffic_for(f"{kern}<2,async,int32>", wl)
+        forms["o2-sync"]["kernel"] = f"{kern}<2,sync,int32>"
+        forms["o2-sync"]["traffic_per_sweep"] = _traffic_for(f"{kern}<2,sync,int32>", wl)
         if name == "caterpillar":
             d_max = B + 1
             bound = math.ceil(math.log(d_max) / math.log(1.5)) + 1
