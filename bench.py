@@ -566,7 +566,7 @@ def variants(cc, g, out, n, m, args, dev, seed, stream, s=None, d=None):
         st = cc.cc_run(g, out, cc.CC_ORDER_AUTO, cc.CC_ASYNC, 0)
         r["schedule"] = [st.order, st.mode, st.check_interval]
         res[f"{args.workload}/learned"] = r
-        cc.cc_sched_load(None)
+        cc.unload_scheduler()
     if s is not None and args.workload.startswith("rmat"):
         # the same graph kept as CSR (native row walk, no edge-list expansion):
         # each edge once in its src row, and stored in both rows (symmetric)
@@ -742,7 +742,7 @@ def batch_compare(cc, G, args, dev, stream, seed):
         res["batched-learned"] = {"ms": ms, "first_call_ms": first, "edges_per_s": total_m / (ms * 1e-3),
                                   "note": "first call includes the feature pass and inference"}
         identical_learned = bool(torch.equal(out_b, ref))
-        cc.cc_sched_load(None)
+        cc.unload_scheduler()
     handles = []
     ps, pd = cc.cc_batch_edges(plan)  # the same (possibly reordered) edges as the batched form
     for g in range(G):

@@ -303,19 +303,29 @@ cc_status cc_batch(int32_t n_graphs, const int64_t *vtx_off, const int64_t *edge
  * order {2, 4, CC_ORDER_FULL}[k/6], mode (k/3)%2 (0 sync, 1 async) and check
  * interval {1, 2, 4}[k%3].
  *
- * A handle (or plan) computes its features and schedule on the first
- * CC_ORDER_AUTO call after weights were loaded and reuses the choice until
- * cc_sched_load is called again (its edges cannot change).
+ * A handle computes its features and schedule once per loaded model (its
+ * edges cannot change).  Its first CC_ORDER_AUTO call does not wait for them:
+ * it enqueues the feature pass and the inference on a stream of the handle's
+ * own (ordered after the work already on the handle's stream) and solves with
+ * the paper's default C-2 (order 2, asynchronous, the caller's check
+ * interval or 1); later calls use the predicted schedule.  A plan computes
+ * the features of all its graphs on its first CC_ORDER_AUTO call, before the
+ * solve.  Every schedule returns the same labels.
  *
  * cc_sched_load        install a weight blob (cc_sched_blob_bytes() bytes, format
  *                      "CCMLP01": header with feature mean/std, then per layer
  *                      BF16 weights [out][in] and FP32 biases); NULL unloads and
  *                      restores the plain order-2 synchronous fallback.  The model
  *                      is process-wide.
+ * cc_sched_load_batch  install the weights that batched solves use (same format;
+ *                      trained on the sweep counts graphs take inside a batch,
+ *                      where a round lasts as long as its slowest graph); NULL
+ *                      unloads them, and batches then use cc_sched_load's model.
  * cc_graph_features / cc_batch_features   features of a graph / every graph of
  *                      a plan (int32 ids), written to HOST memory.
  * cc_sched_predict     classes (and optionally CC_SCHED_CLASSES logits) for
  *                      count HOST feature rows; CC_EINVAL without weights.
+ *                      cc_sched_predict_batch: the same with the batch model.
  * cc_sched_train       train the MLP on the GPU (mini-batch Adam, softmax cross-
  *                      entropy) on N HOST rows with labels in [0, 18); inputs are
  *                      standardised with their own mean/std; parameters start at
@@ -327,12 +337,14 @@ cc_status cc_batch(int32_t n_graphs, const int64_t *vtx_off, const int64_t *edge
  */
 enum { CC_SCHED_FEATURES = 12, CC_SCHED_CLASSES = 18 };
 cc_status cc_sched_load(const void *weights, size_t bytes);
+cc_status cc_sched_load_batch(const void *weights, size_t bytes);
 size_t cc_sched_blob_bytes(void);
 int32_t cc_sched_param_count(void);
 cc_status cc_sched_decode(int32_t cls, int *order, int *mode, int *check_interval);
 cc_status cc_graph_features(cc_graph *g, float *features_out);
 cc_status cc_batch_features(cc_batch_plan *b, float *features_out);
 cc_status cc_sched_predict(const float *features, int32_t count, int32_t *cls_out, float *logits_out);
+cc_status cc_sched_predict_batch(const float *features, int32_t count, int32_t *cls_out, float *logits_out);
 cc_status cc_sched_train(const float *features, const int32_t *labels, int32_t N,
                          const float *init_params, int32_t epochs, int32_t batch, float lr,
                          uint64_t seed, void *blob_out, float *final_loss);

@@ -23,7 +23,7 @@ __all__ = [
     "cc_batch_run", "cc_batch_set_schedule", "cc_batch_run_scheduled", "cc_batch_tuning",
     "cc_batch_set_tuning", "cc_batch_reorder", "cc_batch_edges", "cc_batch_free", "cc_batch", "cc_sched_load", "cc_sched_blob_bytes",
     "cc_sched_param_count", "cc_sched_decode", "cc_graph_features", "cc_batch_features",
-    "cc_sched_predict", "cc_sched_train", "load_default_scheduler", "SCHED_WEIGHTS_PATH", "cc_sched_train_step", "CC_SCHED_FEATURES", "CC_SCHED_CLASSES", "cc_graph_info", "cc_graph_edges", "cc_graph_set_stream", "cc_graph_reorder", "CC_REORDER_SRC", "CC_REORDER_LOWDEG", "CC_REORDER_HUB", "CC_REORDER_DEGREE", "cc_graph_hubs", "cc_graph_perm", "cc_graph_set_launch", "CC_LAUNCH_GRAPH", "CC_LAUNCH_HOST", "cc_strerror",
+    "cc_sched_predict", "cc_sched_predict_batch", "cc_sched_load_batch", "unload_scheduler", "cc_sched_train", "load_default_scheduler", "SCHED_WEIGHTS_PATH", "SCHED_BATCH_WEIGHTS_PATH", "cc_sched_train_step", "CC_SCHED_FEATURES", "CC_SCHED_CLASSES", "cc_graph_info", "cc_graph_edges", "cc_graph_set_stream", "cc_graph_reorder", "CC_REORDER_SRC", "CC_REORDER_LOWDEG", "CC_REORDER_HUB", "CC_REORDER_DEGREE", "cc_graph_hubs", "cc_graph_perm", "cc_graph_set_launch", "CC_LAUNCH_GRAPH", "CC_LAUNCH_HOST", "cc_strerror",
     "cc_last_error",
 ]
 
@@ -366,6 +366,10 @@ lib.cc_batch_features.argtypes = [_p, _p]
 lib.cc_batch_features.restype = _int
 lib.cc_sched_predict.argtypes = [_p, _i32, _p, _p]
 lib.cc_sched_predict.restype = _int
+lib.cc_sched_predict_batch.argtypes = [_p, _i32, _p, _p]
+lib.cc_sched_predict_batch.restype = _int
+lib.cc_sched_load_batch.argtypes = [_p, ctypes.c_size_t]
+lib.cc_sched_load_batch.restype = _int
 lib.cc_sched_train.argtypes = [_p, _p, _i32, _p, _i32, _i32, _f, ctypes.c_uint64, _p, ctypes.POINTER(_f)]
 lib.cc_sched_train.restype = _int
 lib.cc_sched_train_step.argtypes = [_p, _p, _i32, _p, _f, ctypes.POINTER(_f)]
@@ -381,13 +385,35 @@ def cc_sched_load(blob):
     _check(lib.cc_sched_load(buf, len(blob)), "cc_sched_load")
 
 
+def cc_sched_load_batch(blob):
+    """Install the weights batched solves use (bytes); None: batches use the
+    single-graph weights."""
+    if blob is None:
+        _check(lib.cc_sched_load_batch(None, 0), "cc_sched_load_batch")
+        return
+    buf = ctypes.create_string_buffer(bytes(blob), len(blob))
+    _check(lib.cc_sched_load_batch(buf, len(blob)), "cc_sched_load_batch")
+
+
 SCHED_WEIGHTS_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "sched_weights.bin")
+SCHED_BATCH_WEIGHTS_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "sched_weights_batch.bin")
 
 
-def load_default_scheduler(path=None):
-    """Install the committed scheduler weights (written by sched_train.py)."""
+def load_default_scheduler(path=None, batch_path=None):
+    """Install the committed scheduler weights (written by sched_train.py):
+    the single-graph model and, when present, the one for batched solves."""
     with open(path or SCHED_WEIGHTS_PATH, "rb") as f:
         cc_sched_load(f.read())
+    bp = batch_path or SCHED_BATCH_WEIGHTS_PATH
+    if os.path.exists(bp):
+        with open(bp, "rb") as f:
+            cc_sched_load_batch(f.read())
+
+
+def unload_scheduler():
+    """Remove both scheduler models (AUTO falls back to the plain schedule)."""
+    cc_sched_load(None)
+    cc_sched_load_batch(None)
 
 
 def cc_sched_blob_bytes():
@@ -418,13 +444,19 @@ def cc_batch_features(b):
     return out
 
 
-def cc_sched_predict(features):
+def cc_sched_predict(features, batch_model=False):
+    """(classes, logits) of the single-graph model (or of the batch model)."""
     import numpy as np
     f = np.ascontiguousarray(features, dtype=np.float32).reshape(-1, CC_SCHED_FEATURES)
     cls = np.zeros(len(f), dtype=np.int32)
     logits = np.zeros((len(f), CC_SCHED_CLASSES), dtype=np.float32)
-    _check(lib.cc_sched_predict(f.ctypes.data, len(f), cls.ctypes.data, logits.ctypes.data), "cc_sched_predict")
+    fn = lib.cc_sched_predict_batch if batch_model else lib.cc_sched_predict
+    _check(fn(f.ctypes.data, len(f), cls.ctypes.data, logits.ctypes.data), "cc_sched_predict")
     return cls, logits
+
+
+def cc_sched_predict_batch(features):
+    return cc_sched_predict(features, batch_model=True)
 
 
 def cc_sched_train(features, labels, epochs=60, batch=256, lr=2e-3, seed=1, init_params=None):

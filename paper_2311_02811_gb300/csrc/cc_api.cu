@@ -712,8 +712,9 @@ static cc_status run_impl(cc_graph* g, int order, int mode, int c, int32_t max_s
     g_last_error.clear();
     if (!g) return set_error(CC_EINVAL, "cc_run: g is NULL");
     if (g->n > 0 && !labels_out) return set_error(CC_EINVAL, "cc_run: labels_out is NULL");
+    bool defer_features = false;
     if (order == CC_ORDER_AUTO) {
-        cc_status st = cc::resolve_schedule(g, &order, &mode, &c);
+        cc_status st = cc::resolve_schedule(g, &order, &mode, &c, &defer_features);
         if (st != CC_OK) return st;
     }
     const bool schedule = order == CC_ORDER_11MM || order == CC_ORDER_1M1M;
@@ -829,6 +830,12 @@ static cc_status run_impl(cc_graph* g, int order, int mode, int c, int32_t max_s
     if (result != labels_out)
         CC_CUDA(cudaMemcpyAsync(labels_out, result, g->n * B, cudaMemcpyDefault, s));
     CC_CUDA(cudaMemcpyAsync(g->ctl_h, g->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
+    if (defer_features) {
+        // the first CC_ORDER_AUTO call: the scheduler's feature pass goes
+        // behind this solve, on the handle's own stream
+        cc_status st = cc::sched_defer_features(g, s);
+        if (st != CC_OK) return st;
+    }
     unsigned long long cwords[2] = {0, 0};  // compacting runs: edges read and sweeps of the compacting phase
     if (compact) CC_CUDA(cudaMemcpyAsync(cwords, g->clists.cnt + 3, sizeof cwords, cudaMemcpyDeviceToHost, s));
     CC_CUDA(cudaStreamSynchronize(s));

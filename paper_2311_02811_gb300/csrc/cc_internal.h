@@ -49,7 +49,11 @@ bool graph_relabeled(const cc_graph* g);
 
 // CC_ORDER_AUTO: pick (order, mode, check interval) for a graph; the plain
 // order-2 synchronous schedule with c = 1 when no scheduler weights are loaded.
-cc_status resolve_schedule(cc_graph* g, int* order, int* mode, int* c);
+// *deferred: the handle has no prediction for the loaded model yet; the
+// caller solves with the returned default and then calls
+// sched_defer_features, which enqueues the feature pass behind that solve.
+cc_status resolve_schedule(cc_graph* g, int* order, int* mode, int* c, bool* deferred);
+cc_status sched_defer_features(cc_graph* g, cudaStream_t s);
 
 // Batched path (batch.cu) and its schedule resolution (sched.cu).
 cc_status batch_solve(cc_batch_plan* b, int32_t max_sweeps, int32_t* labels_out, int32_t* sweeps_out,

@@ -70,8 +70,9 @@ struct Model {
 
 std::mutex g_mu;
 Model* g_model = nullptr;  // device copy, nullptr when nothing is loaded
-long long g_model_version = 0;  // bumped by every cc_sched_load
-std::vector<unsigned char> g_blob;
+Model* g_model_batch = nullptr;  // weights for batched solves (cc_sched_load_batch), optional
+long long g_model_version = 0;  // bumped by every cc_sched_load / cc_sched_load_batch
+std::vector<unsigned char> g_blob, g_blob_batch;
 
 // ---------------------------------------------------------------------------
 // features
@@ -587,7 +588,7 @@ int nblk(long long items, int threads = 256) { return (int)((items + threads - 1
 // the CUDA host intrinsics so that device and host agree
 __nv_bfloat16 to_bf16(float x) { return __float2bfloat16_rn(x); }
 
-cc_status upload_blob(const unsigned char* blob, size_t bytes) {
+cc_status upload_blob(const unsigned char* blob, size_t bytes, Model** slot, std::vector<unsigned char>* store) {
     if (bytes != kBlobBytes) return cc::set_error(CC_EINVAL, "cc_sched_load: expected %zu bytes, got %zu", kBlobBytes, bytes);
     BlobHeader h;
     std::memcpy(&h, blob, sizeof h);
@@ -613,13 +614,17 @@ cc_status upload_blob(const unsigned char* blob, size_t bytes) {
     take(m.b3, sizeof m.b3);
     take(m.w4, sizeof m.w4);
     take(m.b4, sizeof m.b4);
-    if (!g_model) {
-        cudaError_t e = cudaMalloc(&g_model, sizeof(Model));
+    // a feature pass of another handle may still be reading the old weights
+    // on its side stream
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cc::cuda_fail(e, "cc_sched_load", __FILE__, __LINE__);
+    if (!*slot) {
+        e = cudaMalloc(slot, sizeof(Model));
         if (e != cudaSuccess) return cc::cuda_fail(e, "cc_sched_load", __FILE__, __LINE__);
     }
-    cudaError_t e = cudaMemcpy(g_model, &m, sizeof m, cudaMemcpyHostToDevice);
+    e = cudaMemcpy(*slot, &m, sizeof m, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return cc::cuda_fail(e, "cc_sched_load", __FILE__, __LINE__);
-    g_blob.assign(blob, blob + bytes);
+    store->assign(blob, blob + bytes);
     return CC_OK;
 }
 
@@ -642,14 +647,27 @@ struct SchedCtx {
     float* d_feat = nullptr;   // G x kFeat
     int32_t* d_cls = nullptr;  // G
     std::vector<int32_t> h_cls;  // host copy of the classes
-    std::vector<int64_t> h_off;  // offsets, re-sent before each use when shared
+    std::vector<int64_t> h_off;  // offsets of a single graph, sent before each feature pass
     long long version = -1;    // model version h_cls was computed with
-    bool shared = false;       // device buffers belong to the process (G == 1)
+    // single graphs: the feature pass runs on a stream of its own while the
+    // first CC_ORDER_AUTO call solves with the default schedule
+    void* block = nullptr;     // d_off, d_feat and d_cls of a single graph in one allocation
+    cudaStream_t side = nullptr;
+    cudaEvent_t ready = nullptr, done = nullptr;
+    long long pending = -1;    // model version of a feature pass enqueued on side
 };
 
 void sched_ctx_free(SchedCtx* c) {
     if (!c) return;
-    if (!c->shared) {
+    if (c->side) {
+        cudaStreamSynchronize(c->side);  // a feature pass may still read the edges
+        cudaStreamDestroy(c->side);
+    }
+    if (c->ready) cudaEventDestroy(c->ready);
+    if (c->done) cudaEventDestroy(c->done);
+    if (c->block) {
+        cc::dfree(c->block, nullptr);  // the side stream has finished
+    } else {
         cudaFree(c->d_off);
         cudaFree(c->d_feat);
         cudaFree(c->d_cls);
@@ -696,31 +714,25 @@ cc_status scratch_get(int ctas, cudaStream_t s) {
     return CC_OK;
 }
 
-// Device buffers shared by every single-graph context (used under g_mu).
-int64_t* g_one_off = nullptr;
-float* g_one_feat = nullptr;
-int32_t* g_one_cls = nullptr;
-
 cc_status ctx_get(cc::SchedCtx** slot, int32_t G, const int64_t* off_v, const int64_t* off_e, cudaStream_t s) {
     if (*slot) return CC_OK;
     cc::SchedCtx* c = new (std::nothrow) cc::SchedCtx();
     if (!c) return cc::set_error(CC_ENOMEM, "scheduler context");
     c->G = G;
     if (G == 1) {
-        // a handle has one graph: no allocation of its own
-        if (!g_one_off) {
-            cudaError_t e = cudaMalloc(&g_one_off, 4 * sizeof(int64_t));
-            if (e == cudaSuccess) e = cudaMalloc(&g_one_feat, kFeat * sizeof(float));
-            if (e == cudaSuccess) e = cudaMalloc(&g_one_cls, 4 * sizeof(int32_t));
-            if (e != cudaSuccess) {
-                delete c;
-                return cc::cuda_fail(e, "scheduler buffers", __FILE__, __LINE__);
-            }
+        // a handle has one graph: 4 offsets, the features and the class in
+        // one small block, and a stream for the background feature pass
+        cudaError_t e = cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cc::dmalloc(&c->block, 4 * sizeof(int64_t) + 16 * sizeof(float) + 4 * sizeof(int32_t), c->side);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ready, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->done, cudaEventDisableTiming);
+        if (e != cudaSuccess) {
+            cc::sched_ctx_free(c);
+            return cc::cuda_fail(e, "scheduler buffers", __FILE__, __LINE__);
         }
-        c->shared = true;
-        c->d_off = g_one_off;
-        c->d_feat = g_one_feat;
-        c->d_cls = g_one_cls;
+        c->d_off = static_cast<int64_t*>(c->block);
+        c->d_feat = reinterpret_cast<float*>(c->d_off + 4);
+        c->d_cls = reinterpret_cast<int32_t*>(c->d_feat + 16);
         c->h_cls.assign(1, 0);
         c->h_off = {off_v[0], off_v[1], off_e[0], off_e[1]};
         *slot = c;
@@ -786,8 +798,9 @@ void decode(int32_t k, int* order, int* mode, int* c) {
 }
 
 // predict classes for G feature rows already on the device
-cc_status predict_device(const float* d_feats, int32_t G, int32_t* d_cls, float* d_logits, cudaStream_t s) {
-    mlp_infer_kernel<<<(G + 7) / 8, 256, 0, s>>>(g_model, d_feats, G, d_cls, d_logits);
+cc_status predict_device(const Model* model, const float* d_feats, int32_t G, int32_t* d_cls, float* d_logits,
+                         cudaStream_t s) {
+    mlp_infer_kernel<<<(G + 7) / 8, 256, 0, s>>>(model, d_feats, G, d_cls, d_logits);
     SCUDA(cudaGetLastError());
     return CC_OK;
 }
@@ -811,6 +824,7 @@ static cc_status handle_features(cc_graph* g, cudaStream_t s) {
         const int64_t ov[2] = {0, n}, oe[2] = {0, S};
         cc_status st = ctx_get(slot, 1, ov, oe, s);
         if (st != CC_OK) return st;
+        (*slot)->h_off = {0, n, 0, S};  // the feature pass reads the S decoded pairs
         int32_t* pairs = nullptr;
         SCUDA(cc::dmalloc(reinterpret_cast<void**>(&pairs), (size_t)(2 * S + 1) * sizeof(int32_t), s));
         cc::hub_sample_kernel<<<(int)((S + 255) / 256), 256, 0, s>>>(
@@ -829,6 +843,7 @@ static cc_status handle_features(cc_graph* g, cudaStream_t s) {
         const int64_t ov[2] = {0, n}, oe[2] = {0, m};
         cc_status st = ctx_get(slot, 1, ov, oe, s);
         if (st != CC_OK) return st;
+        (*slot)->h_off = {0, n, 0, m};
         return run_features(*slot, static_cast<const int32_t*>(cc::graph_src(g)),
                             static_cast<const int32_t*>(cc::graph_dst(g)), s);
     }
@@ -836,6 +851,7 @@ static cc_status handle_features(cc_graph* g, cudaStream_t s) {
     const int64_t ov[2] = {0, n}, oe[2] = {0, S};
     cc_status st = ctx_get(slot, 1, ov, oe, s);
     if (st != CC_OK) return st;
+    (*slot)->h_off = {0, n, 0, S};  // the feature pass reads the S sampled entries
     int32_t* pairs = nullptr;
     SCUDA(cc::dmalloc(reinterpret_cast<void**>(&pairs), (size_t)(2 * S + 1) * sizeof(int32_t), s));
     if (S > 0) {
@@ -854,7 +870,7 @@ static cc_status handle_features(cc_graph* g, cudaStream_t s) {
 
 namespace cc {
 
-cc_status resolve_schedule(cc_graph* g, int* order, int* mode, int* c) {
+cc_status resolve_schedule(cc_graph* g, int* order, int* mode, int* c, bool* deferred) {
     std::lock_guard<std::mutex> lock(g_mu);
     const int want_c = *c;
     if (!g_model) {  // plain order-2 synchronous schedule
@@ -869,25 +885,59 @@ cc_status resolve_schedule(cc_graph* g, int* order, int* mode, int* c) {
         *c = want_c < 1 ? 1 : want_c;
         return CC_OK;
     }
-    cudaStream_t s = graph_stream(g);
+    // The edges of a handle never change: the choice is made once per model.
+    // The first call does not wait for it: it solves with the paper's default
+    // C-2 (order 2, asynchronous) and asks the caller to enqueue the feature
+    // pass and the inference behind the solve (sched_defer_features); the
+    // next call takes the predicted schedule.  Every schedule returns the
+    // same labels.
     SchedCtx** slot = graph_sched_slot(g);
-    // the edges of a handle never change: the choice is made once per model
-    if (!*slot || (*slot)->version != g_model_version) {
-        cc_status st = handle_features(g, s);
-        if (st != CC_OK) return st;
-        SchedCtx* x = *slot;
-        st = predict_device(x->d_feat, 1, x->d_cls, nullptr, s);
-        if (st == CC_OK) {
-            cudaError_t e = cudaMemcpyAsync(x->h_cls.data(), x->d_cls, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
-            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-            if (e != cudaSuccess) st = cuda_fail(e, "sched", __FILE__, __LINE__);
-        }
-        if (st != CC_OK) return st;
+    SchedCtx* x = *slot;
+    if (!x || (x->version != g_model_version && x->pending != g_model_version)) {
+        *order = 2;
+        *mode = CC_ASYNC;
+        *c = want_c < 1 ? 1 : want_c;
+        if (deferred) *deferred = true;
+        return CC_OK;
+    }
+    if (x->version != g_model_version) {  // the feature pass enqueued by an earlier call
+        cudaError_t e = cudaMemcpyAsync(x->h_cls.data(), x->d_cls, sizeof(int32_t), cudaMemcpyDeviceToHost, x->side);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(x->side);
+        if (e != cudaSuccess) return cuda_fail(e, "sched", __FILE__, __LINE__);
         x->version = g_model_version;
     }
     int cc_ = 1;
-    decode((*slot)->h_cls[0], order, mode, &cc_);
+    decode(x->h_cls[0], order, mode, &cc_);
     *c = want_c >= 1 ? want_c : cc_;
+    return CC_OK;
+}
+
+// The feature pass and the inference of a handle, on the handle's own
+// stream, ordered after everything the caller has enqueued on s so far (the
+// solve of the first CC_ORDER_AUTO call): they run after that solve on the
+// GPU, and the host returns without waiting for them.
+cc_status sched_defer_features(cc_graph* g, cudaStream_t s) {
+    std::lock_guard<std::mutex> lock(g_mu);
+    if (!g_model) return CC_OK;
+    SchedCtx** slot = graph_sched_slot(g);
+    if (!*slot) {
+        long long n = 0, m = 0;
+        graph_nm(g, &n, &m);
+        const int64_t ov[2] = {0, n}, oe[2] = {0, m};
+        cc_status st = ctx_get(slot, 1, ov, oe, s);
+        if (st != CC_OK) return st;
+    }
+    SchedCtx* x = *slot;
+    if (x->pending == g_model_version || x->version == g_model_version) return CC_OK;
+    cudaError_t e = cudaEventRecord(x->ready, s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(x->side, x->ready, 0);
+    if (e != cudaSuccess) return cuda_fail(e, "sched", __FILE__, __LINE__);
+    cc_status st = handle_features(g, x->side);
+    if (st == CC_OK) st = predict_device(g_model, x->d_feat, 1, x->d_cls, nullptr, x->side);
+    if (st != CC_OK) return st;
+    e = cudaEventRecord(x->done, x->side);
+    if (e != cudaSuccess) return cuda_fail(e, "sched", __FILE__, __LINE__);
+    x->pending = g_model_version;
     return CC_OK;
 }
 
@@ -896,7 +946,9 @@ cc_status batch_resolve_schedule(cc_batch_plan* b, int mode, int c) {
     const int32_t G = batch_graph_count(b);
     std::vector<int32_t> h(G, 2), sync(G, 1), cv(G, c < 1 ? 1 : c);
     std::lock_guard<std::mutex> lock(g_mu);
-    if (g_model && G > 0) {
+    // weights trained for batched solves when loaded, else the single-graph ones
+    const Model* model = g_model_batch ? g_model_batch : g_model;
+    if (model && G > 0) {
         cudaStream_t s = batch_stream(b);
         SchedCtx** slot = batch_sched_slot(b);
         cc_status st = ctx_get(slot, G, batch_off_v(b), batch_off_e(b), s);
@@ -904,7 +956,7 @@ cc_status batch_resolve_schedule(cc_batch_plan* b, int mode, int c) {
         SchedCtx* x = *slot;
         if (x->version != g_model_version) {
             st = run_features(x, batch_src(b), batch_dst(b), s);
-            if (st == CC_OK) st = predict_device(x->d_feat, G, x->d_cls, nullptr, s);
+            if (st == CC_OK) st = predict_device(model, x->d_feat, G, x->d_cls, nullptr, s);
             if (st == CC_OK) {
                 cudaError_t e = cudaMemcpyAsync(x->h_cls.data(), x->d_cls, G * sizeof(int32_t), cudaMemcpyDeviceToHost, s);
                 if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -936,16 +988,24 @@ cc_status batch_resolve_schedule(cc_batch_plan* b, int mode, int c) {
 // C ABI
 // ---------------------------------------------------------------------------
 
-extern "C" cc_status cc_sched_load(const void* weights, size_t bytes) {
+static cc_status load_into(const void* weights, size_t bytes, Model** slot, std::vector<unsigned char>* store) {
     std::lock_guard<std::mutex> lock(g_mu);
     ++g_model_version;
     if (!weights) {
-        if (g_model) cudaFree(g_model);
-        g_model = nullptr;
-        g_blob.clear();
+        if (*slot) cudaFree(*slot);  // waits for work that may still read it
+        *slot = nullptr;
+        store->clear();
         return CC_OK;
     }
-    return upload_blob(static_cast<const unsigned char*>(weights), bytes);
+    return upload_blob(static_cast<const unsigned char*>(weights), bytes, slot, store);
+}
+
+extern "C" cc_status cc_sched_load(const void* weights, size_t bytes) {
+    return load_into(weights, bytes, &g_model, &g_blob);
+}
+
+extern "C" cc_status cc_sched_load_batch(const void* weights, size_t bytes) {
+    return load_into(weights, bytes, &g_model_batch, &g_blob_batch);
 }
 
 extern "C" size_t cc_sched_blob_bytes(void) { return kBlobBytes; }
@@ -964,6 +1024,10 @@ extern "C" cc_status cc_graph_features(cc_graph* g, float* features_out) {
     std::lock_guard<std::mutex> lock(g_mu);
     cudaStream_t s = cc::graph_stream(g);
     cc::SchedCtx** slot = cc::graph_sched_slot(g);
+    if (*slot && (*slot)->side) {  // a background feature pass writes the same buffers
+        cudaError_t e = cudaStreamSynchronize((*slot)->side);
+        if (e != cudaSuccess) return cc::cuda_fail(e, "cc_graph_features", __FILE__, __LINE__);
+    }
     cc_status st = handle_features(g, s);
     if (st != CC_OK) return st;
     cudaError_t e = cudaMemcpyAsync(features_out, (*slot)->d_feat, kFeat * sizeof(float), cudaMemcpyDeviceToHost, s);
@@ -990,10 +1054,12 @@ extern "C" cc_status cc_batch_features(cc_batch_plan* b, float* features_out) {
     return CC_OK;
 }
 
-extern "C" cc_status cc_sched_predict(const float* features, int32_t count, int32_t* cls_out, float* logits_out) {
+static cc_status predict_host(const float* features, int32_t count, int32_t* cls_out, float* logits_out,
+                              bool batch_model) {
     if (count < 0 || (count > 0 && (!features || !cls_out))) return cc::set_error(CC_EINVAL, "cc_sched_predict: bad arguments");
     std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_model) return cc::set_error(CC_EINVAL, "cc_sched_predict: no scheduler weights loaded");
+    if (!(batch_model ? g_model_batch : g_model))
+        return cc::set_error(CC_EINVAL, "cc_sched_predict: no scheduler weights loaded");
     if (count == 0) return CC_OK;
     float* d_f = nullptr;
     int32_t* d_c = nullptr;
@@ -1003,7 +1069,7 @@ extern "C" cc_status cc_sched_predict(const float* features, int32_t count, int3
     if (e == cudaSuccess) e = cudaMalloc(&d_l, (size_t)count * kOut * sizeof(float));
     if (e == cudaSuccess) e = cudaMemcpy(d_f, features, (size_t)count * kFeat * sizeof(float), cudaMemcpyHostToDevice);
     cc_status st = e == cudaSuccess ? CC_OK : cc::cuda_fail(e, "cc_sched_predict", __FILE__, __LINE__);
-    if (st == CC_OK) st = predict_device(d_f, count, d_c, d_l, nullptr);
+    if (st == CC_OK) st = predict_device(batch_model ? g_model_batch : g_model, d_f, count, d_c, d_l, nullptr);
     if (st == CC_OK) {
         e = cudaMemcpy(cls_out, d_c, (size_t)count * sizeof(int32_t), cudaMemcpyDeviceToHost);
         if (e == cudaSuccess && logits_out)
@@ -1014,6 +1080,15 @@ extern "C" cc_status cc_sched_predict(const float* features, int32_t count, int3
     cudaFree(d_c);
     cudaFree(d_l);
     return st;
+}
+
+extern "C" cc_status cc_sched_predict(const float* features, int32_t count, int32_t* cls_out, float* logits_out) {
+    return predict_host(features, count, cls_out, logits_out, false);
+}
+
+extern "C" cc_status cc_sched_predict_batch(const float* features, int32_t count, int32_t* cls_out,
+                                            float* logits_out) {
+    return predict_host(features, count, cls_out, logits_out, true);
 }
 
 // Train the MLP from scratch (or from init_blob) on N labelled feature rows;

@@ -12,6 +12,13 @@ log-uniform n in [1e3, 1e6]):
      near-ties do not turn measurement noise into label noise.
 Then train the MLP on the GPU (cc_sched_train) and write the weight blob.
 
+A second model serves batched solves (cc_sched_load_batch).  Inside a batch
+a round lasts as long as its slowest graph and every graph is checked after
+every sweep, so its label is the asynchronous order (2, 4 or the full chain)
+with which the graph took the fewest sweeps in a batched solve of its chunk
+(after cc_batch_reorder, as batched solves run), ties going to the faster
+single-graph schedule.
+
 Held-out evaluation: graphs drawn from another seed plus large R-MAT (up to
 scale 25), grid, path and caterpillar graphs; each is solved with
   plain    order 2, synchronous, c = 1 (the library's fallback schedule),
@@ -65,15 +72,38 @@ def time_schedules(n, s, d, reps=2):
     return times
 
 
+# the classes a batch can use: order 2, 4 or the full chain, asynchronous
+# (a batch checks every graph after every sweep)
+BATCH_CLASSES = (3, 9, 15)
+
+
+def batch_sweeps(plan, out):
+    """Sweeps each graph of a plan takes in a batched solve with each of the
+    BATCH_CLASSES schedules (G x 3)."""
+    cols = []
+    for k in BATCH_CLASSES:
+        order, mode, c = cc.cc_sched_decode(k)
+        sw, _ = cc.cc_batch_run(plan, out, order, mode, c)
+        cols.append(np.asarray(sw))
+    return np.stack(cols, axis=1)
+
+
 def build_training_set(n_graphs, chunk, log):
-    feats, all_times = [], []
+    feats, all_times, bfeats, bsweeps = [], [], [], []
     done = 0
     while done < n_graphs:
         cnt = min(chunk, n_graphs - done)
         vo, eo, s, d, _ = gg.batch_mix(cnt, seed=gg.stream_key(TRAIN_SEED, done), device="cuda")
         plan = cc.cc_batch_init(vo, eo, s, d)
         F = cc.cc_batch_features(plan)
+        # the batch objective: sweeps inside a batched solve, on the edge order
+        # batched solves use (cc_batch_reorder)
+        cc.cc_batch_reorder(plan)
+        bfeats.append(cc.cc_batch_features(plan))
+        out = torch.empty(int(vo[-1]), dtype=torch.int32, device="cuda")
+        bsweeps.append(batch_sweeps(plan, out))
         cc.cc_batch_free(plan)
+        del out
         for g in range(cnt):
             a, b = int(eo[g]), int(eo[g + 1])
             t = time_schedules(int(vo[g + 1] - vo[g]), s[a:b], d[a:b])
@@ -84,7 +114,42 @@ def build_training_set(n_graphs, chunk, log):
         torch.cuda.empty_cache()
         log(f"training graphs: {done}/{n_graphs}")
     T = np.array(all_times)
-    return np.array(feats, np.float32), label_times(T), T
+    Sw = np.concatenate(bsweeps)
+    return (np.array(feats, np.float32), label_times(T), T, np.concatenate(bfeats).astype(np.float32),
+            label_batch(Sw, T), Sw)
+
+
+def label_batch(Sw, T):
+    """Batch label: the schedule with the fewest sweeps inside the batch (a
+    round lasts as long as its slowest graph); ties go to the schedule whose
+    single-graph solve was faster."""
+    cand = np.array(BATCH_CLASSES)
+    key = Sw.astype(np.float64) * 1e6 + T[:, cand] / T[:, cand].max(axis=1, keepdims=True)
+    return cand[np.argmin(key, axis=1)].astype(np.int32)
+
+
+def evaluate_batch(n_mix, log, reps=3):
+    """The held-out mix as one batch (reordered): each fixed batch schedule
+    and the learned per-graph schedule, device time per solve."""
+    vo, eo, s, d, _ = gg.batch_mix(n_mix, seed=HELDOUT_SEED, device="cuda")
+    plan = cc.cc_batch_init(vo, eo, s, d, autotune=1)
+    cc.cc_batch_reorder(plan)
+    out = torch.empty(int(vo[-1]), dtype=torch.int32, device="cuda")
+    res = {}
+    ref = None
+    for name, (order, mode, c) in (("batched-c2", (2, cc.CC_ASYNC, 1)), ("batched-o4", (4, cc.CC_ASYNC, 1)),
+                                   ("batched-full", (cc.CC_ORDER_FULL, cc.CC_ASYNC, 1)),
+                                   ("batched-plain", (2, cc.CC_SYNC, 1)),
+                                   ("batched-learned", (cc.CC_ORDER_AUTO, cc.CC_ASYNC, 0))):
+        cc.cc_batch_run(plan, out, order, mode, c)
+        res[name] = min(cc.cc_batch_run(plan, out, order, mode, c)[1] for _ in range(reps))
+        if ref is None:
+            ref = out.clone()
+        elif not torch.equal(ref, out):
+            raise RuntimeError("batched schedules disagree on the labels")
+    cc.cc_batch_free(plan)
+    log(f"held-out batch ({n_mix} graphs): {res}")
+    return res
 
 
 def label_times(T, tol=1.03):
@@ -163,6 +228,7 @@ def main():
     ap.add_argument("--chunk", type=int, default=500)
     ap.add_argument("--epochs", type=int, default=80)
     ap.add_argument("--out", default=os.path.join(HERE, "sched_weights.bin"))
+    ap.add_argument("--out-batch", default=os.path.join(HERE, "sched_weights_batch.bin"))
     ap.add_argument("--report", default=os.path.join(os.path.dirname(HERE), "profiles", "sched_weights.json"))
     ap.add_argument("--dump", default="", help="also save features, labels and timings (.npz)")
     ap.add_argument("--eval-only", action="store_true",
@@ -175,8 +241,8 @@ def main():
 
     torch.cuda.set_device(0)
     if args.eval_only:
-        with open(args.out, "rb") as f:
-            cc.cc_sched_load(f.read())
+        cc.load_default_scheduler(args.out, args.out_batch)
+        batch_eval = evaluate_batch(args.heldout, log)
         rows, tot = evaluate(args.heldout, log)
         report = json.load(open(args.report)) if os.path.exists(args.report) else {}
         report.update({"heldout_totals_ms": tot,
@@ -185,13 +251,14 @@ def main():
                        "heldout_first_call_speedup_vs_plain": tot["plain_first_ms"] / tot["learned_first_ms"],
                        "heldout_first_call_speedup_vs_c2": tot["c2_first_ms"] / tot["learned_first_ms"],
                        "heldout_all_identical": all(r["identical"] for r in rows), "heldout": rows})
+        report.setdefault("batch_model", {})["heldout_batch_ms"] = batch_eval
         with open(args.report, "w") as f:
             json.dump(report, f, indent=0, separators=(",", ":"))
         log(f"updated {args.report}")
         return
-    X, y, T = build_training_set(args.train, args.chunk, log)
+    X, y, T, Xb, yb, Sw = build_training_set(args.train, args.chunk, log)
     if args.dump:
-        np.savez_compressed(args.dump, X=X, y=y, T=T)
+        np.savez_compressed(args.dump, X=X, y=y, T=T, Xb=Xb, yb=yb, Sw=Sw)
     # 90/10 split for a validation accuracy; the final model trains on all rows
     idx = np.arange(len(y))
     val = idx % 10 == 0
@@ -206,6 +273,20 @@ def main():
     log(f"trained: loss {loss:.4f}, validation accuracy {val_acc:.3f}, mean time ratio to best {regret:.3f}")
     with open(args.out, "wb") as f:
         f.write(blob)
+    # the batch model: same features (after cc_batch_reorder), batch labels
+    blob_b, loss_b = cc.cc_sched_train(Xb[~val], yb[~val], epochs=args.epochs, batch=256, lr=2e-3, seed=8)
+    cc.cc_sched_load_batch(blob_b)
+    pred_b, _ = cc.cc_sched_predict_batch(Xb[val])
+    val_acc_b = float((pred_b == yb[val]).mean())
+    col = {k: i for i, k in enumerate(BATCH_CLASSES)}
+    Swv = Sw[val]
+    sweeps_ratio_b = float(Swv[np.arange(val.sum()), [col.get(int(k), 2) for k in pred_b]].sum() / Swv.min(axis=1).sum())
+    blob_b, loss_b = cc.cc_sched_train(Xb, yb, epochs=args.epochs, batch=256, lr=2e-3, seed=8)
+    cc.cc_sched_load_batch(blob_b)
+    with open(args.out_batch, "wb") as f:
+        f.write(blob_b)
+    log(f"batch model: loss {loss_b:.4f}, validation accuracy {val_acc_b:.3f}, sweeps vs fewest {sweeps_ratio_b:.3f}")
+    batch_eval = evaluate_batch(args.heldout, log)
     rows, tot = evaluate(args.heldout, log)
     label_hist = np.bincount(y, minlength=cc.CC_SCHED_CLASSES).tolist()
     report = {"train_graphs": int(len(y)), "label_histogram": label_hist, "final_loss": loss,
@@ -216,10 +297,14 @@ def main():
               "heldout_first_call_speedup_vs_plain": tot["plain_first_ms"] / tot["learned_first_ms"],
               "heldout_first_call_speedup_vs_c2": tot["c2_first_ms"] / tot["learned_first_ms"],
               "heldout_all_identical": all(r["identical"] for r in rows),
+              "batch_model": {"label_histogram": np.bincount(yb, minlength=cc.CC_SCHED_CLASSES).tolist(),
+                              "final_loss": loss_b, "validation_accuracy": val_acc_b,
+                              "validation_sweeps_ratio_to_fewest": sweeps_ratio_b,
+                              "heldout_batch_ms": batch_eval},
               "heldout": rows}
     with open(args.report, "w") as f:
         json.dump(report, f, indent=0, separators=(",", ":"))
-    log(f"wrote {args.out} and {args.report}")
+    log(f"wrote {args.out}, {args.out_batch} and {args.report}")
 
 
 if __name__ == "__main__":

@@ -186,7 +186,7 @@ def test_relabel_rejections_and_auto(cc):
     try:
         cc.cc_run(g, out, cc.CC_ORDER_AUTO, cc.CC_ASYNC, 0)
     finally:
-        cc.cc_sched_load(None)
+        cc.unload_scheduler()
     assert np.array_equal(out.cpu().numpy(), oracle.uf_labels(n, s, d))
     for launch in (cc.CC_LAUNCH_HOST, cc.CC_LAUNCH_GRAPH):
         cc.cc_graph_set_launch(g, launch)

@@ -168,3 +168,86 @@ def test_auto_schedule_returns_exact_labels(cc):
     assert (st.order, st.mode, st.check_interval) == (2, cc.CC_SYNC, 1)
     _, it, _, _ = oracle.contour_sync(n, s, d, 2)
     assert st.sweeps == it
+
+
+def _constant_blob(cls):
+    """A weight blob whose output is the one-hot bias of class cls whatever
+    the features (every weight zero)."""
+    rng = np.random.default_rng(0)
+    blob = bytearray(_random_blob(rng))
+    import struct
+    hdr = 8 + 16 + 2 * 4 * 12
+    off = hdr
+    for li, (ni, no) in enumerate(zip(so.LAYER_IN, so.LAYER_OUT)):
+        blob[off:off + 2 * ni * no] = bytes(2 * ni * no)  # bf16 zeros
+        off += 2 * ni * no
+        bias = np.zeros(no, np.float32)
+        if li == len(so.LAYER_IN) - 1:
+            bias[cls] = 1.0
+        blob[off:off + 4 * no] = bias.tobytes()
+        off += 4 * no
+    assert off == len(blob)
+    return bytes(blob)
+
+
+@pytest.mark.parametrize("layout", ["plain", "hub", "degree", "csr"])
+def test_auto_first_call_uses_default_then_prediction(cc, layout):
+    """The first CC_ORDER_AUTO call of a handle solves with C-2 while the
+    feature pass runs on a side stream; the next call uses the class the
+    model predicts from exactly the features cc_graph_features returns."""
+    rng = np.random.default_rng(21)
+    cc.cc_sched_load(_random_blob(rng))
+    try:
+        n, s, d = GRAPHS["rmat16-sampled"]()
+        want = oracle.uf_labels(n, s, d)
+        if layout == "csr":
+            off, cols = gg.to_csr(n, s, d)
+            g = cc.cc_init(n, off.cuda(), cols.cuda(), m=cols.numel(), id_bits=32, layout=cc.CC_CSR_NATIVE,
+                           on_device=True)
+        else:
+            g = cc.cc_init(n, s.cuda(), d.cuda())
+            if layout != "plain":
+                cc.cc_graph_reorder(g, cc.CC_REORDER_HUB if layout == "hub" else cc.CC_REORDER_DEGREE)
+        out = torch.empty(n, dtype=torch.int32, device="cuda")
+        st = cc.cc_run(g, out, cc.CC_ORDER_AUTO, cc.CC_ASYNC, 0)
+        assert (st.order, st.mode, st.check_interval) == (2, cc.CC_ASYNC, 1)
+        assert np.array_equal(out.cpu().numpy(), want)
+        out.fill_(-1)
+        st2 = cc.cc_run(g, out, cc.CC_ORDER_AUTO, cc.CC_ASYNC, 0)
+        assert np.array_equal(out.cpu().numpy(), want)
+        cls, _ = cc.cc_sched_predict(cc.cc_graph_features(g))
+        assert (st2.order, st2.mode, st2.check_interval) == cc.cc_sched_decode(int(cls[0]))
+        cc.cc_free(g)
+        # a handle freed while its feature pass may still run
+        g = cc.cc_init(n, s.cuda(), d.cuda())
+        cc.cc_run(g, out, cc.CC_ORDER_AUTO, cc.CC_ASYNC, 0)
+        cc.cc_free(g)
+    finally:
+        cc.cc_sched_load(None)
+
+
+def test_batch_weights_take_precedence(cc):
+    """cc_sched_load_batch installs the weights batched solves use; without
+    them a batch uses the single-graph weights.  Synchronous sweep counts are
+    deterministic, so the schedule each graph ran is visible in them."""
+    vo, eo, s, d, _ = gg.batch_mix(24, seed=22, device="cuda", n_lo=300, n_hi=3e4)
+    b = cc.cc_batch_init(vo, eo, s, d)
+    out = torch.empty(int(vo[-1]), dtype=torch.int32, device="cuda")
+    o2, _ = cc.cc_batch_run(b, out, 2, cc.CC_SYNC, 1)
+    ref = out.clone()
+    o4, _ = cc.cc_batch_run(b, out, 4, cc.CC_SYNC, 1)
+    assert not np.array_equal(o2, o4)
+    try:
+        cc.cc_sched_load(_constant_blob(6))        # order 4, synchronous
+        cc.cc_sched_load_batch(_constant_blob(0))  # order 2, synchronous
+        x = cc.cc_batch_features(b)
+        assert (cc.cc_sched_predict(x)[0] == 6).all() and (cc.cc_sched_predict_batch(x)[0] == 0).all()
+        sw, _ = cc.cc_batch_run(b, out, cc.CC_ORDER_AUTO, cc.CC_ASYNC, 0)
+        assert np.array_equal(sw, o2) and torch.equal(out, ref)
+        cc.cc_sched_load_batch(None)
+        sw, _ = cc.cc_batch_run(b, out, cc.CC_ORDER_AUTO, cc.CC_ASYNC, 0)
+        assert np.array_equal(sw, o4) and torch.equal(out, ref)
+    finally:
+        cc.cc_sched_load(None)
+        cc.cc_sched_load_batch(None)
+        cc.cc_batch_free(b)
