@@ -14,10 +14,12 @@ Then train the MLP on the GPU (cc_sched_train) and write the weight blob.
 
 A second model serves batched solves (cc_sched_load_batch).  Inside a batch
 a round lasts as long as its slowest graph and every graph is checked after
-every sweep, so its label is the asynchronous order (2, 4 or the full chain)
-with which the graph took the fewest sweeps in a batched solve of its chunk
-(after cc_batch_reorder, as batched solves run), ties going to the faster
-single-graph schedule.
+every sweep, so a graph's share of the batch is its sweep count times what
+a sweep of its edges costs with the chosen order.  Its label is the
+asynchronous order (2, 4 or the full chain) minimising that product: sweeps
+as measured in a batched solve of the graph's chunk (after cc_batch_reorder,
+as batched solves run), cost per swept edge from the same batches' device
+times.
 
 Held-out evaluation: graphs drawn from another seed plus large R-MAT (up to
 scale 25), grid, path and caterpillar graphs; each is solved with
@@ -77,33 +79,69 @@ def time_schedules(n, s, d, reps=2):
 BATCH_CLASSES = (3, 9, 15)
 
 
-def batch_sweeps(plan, out):
-    """Sweeps each graph of a plan takes in a batched solve with each of the
-    BATCH_CLASSES schedules (G x 3)."""
-    cols = []
+def batch_runs(plan, out):
+    """Each BATCH_CLASSES schedule on a plan: the sweeps of every graph (G x 3)
+    and the batch's device time per solve (3,), the faster of two runs."""
+    cols, ms = [], []
     for k in BATCH_CLASSES:
         order, mode, c = cc.cc_sched_decode(k)
-        sw, _ = cc.cc_batch_run(plan, out, order, mode, c)
+        cc.cc_batch_run(plan, out, order, mode, c)
+        sw, t = cc.cc_batch_run(plan, out, order, mode, c)
         cols.append(np.asarray(sw))
-    return np.stack(cols, axis=1)
+        ms.append(t)
+    return np.stack(cols, axis=1), np.array(ms)
+
+
+def build_batch_set(n_graphs, chunk, log):
+    """Features (after cc_batch_reorder, as batched solves run) and, for every
+    graph, the sweeps it took in a batched solve of its chunk with each
+    BATCH_CLASSES schedule; per chunk, the batch time of each schedule and
+    the sum over its graphs of sweeps x edges."""
+    feats, sweeps, ms_all, swm_all = [], [], [], []
+    done = 0
+    while done < n_graphs:
+        cnt = min(chunk, n_graphs - done)
+        vo, eo, s, d, _ = gg.batch_mix(cnt, seed=gg.stream_key(TRAIN_SEED, done), device="cuda")
+        plan = cc.cc_batch_init(vo, eo, s, d)
+        cc.cc_batch_reorder(plan)
+        feats.append(cc.cc_batch_features(plan))
+        out = torch.empty(int(vo[-1]), dtype=torch.int32, device="cuda")
+        sw, ms = batch_runs(plan, out)
+        cc.cc_batch_free(plan)
+        m = np.diff(eo).astype(np.float64)
+        sweeps.append(sw)
+        ms_all.append(ms)
+        swm_all.append((sw * m[:, None]).sum(axis=0))
+        done += cnt
+        del s, d, out
+        torch.cuda.empty_cache()
+    log(f"batch training graphs: {done}")
+    return (np.concatenate(feats).astype(np.float32), np.concatenate(sweeps), np.array(ms_all),
+            np.array(swm_all))
+
+
+def label_batch(Sw, ms, swm):
+    """Batch label: the schedule with which the graph took the fewest sweeps
+    in its batched solve (a round lasts as long as its slowest graph); at
+    equal sweeps, the schedule whose training batches ran fastest overall.
+    A cost-per-swept-edge label was tried and lost on held-out batches: a
+    wrongly cheaper order that needs one more sweep lengthens its whole wave,
+    which costs more than a cheaper sweep saves."""
+    total = ms.sum(axis=0)
+    rank = np.argsort(np.argsort(total))  # 0 = fastest over the training batches
+    key = Sw * len(BATCH_CLASSES) + rank[None, :]
+    return np.array(BATCH_CLASSES)[np.argmin(key, axis=1)].astype(np.int32), total / swm.sum(axis=0)
 
 
 def build_training_set(n_graphs, chunk, log):
-    feats, all_times, bfeats, bsweeps = [], [], [], []
+    feats, all_times = [], []
     done = 0
     while done < n_graphs:
         cnt = min(chunk, n_graphs - done)
         vo, eo, s, d, _ = gg.batch_mix(cnt, seed=gg.stream_key(TRAIN_SEED, done), device="cuda")
         plan = cc.cc_batch_init(vo, eo, s, d)
         F = cc.cc_batch_features(plan)
-        # the batch objective: sweeps inside a batched solve, on the edge order
-        # batched solves use (cc_batch_reorder)
-        cc.cc_batch_reorder(plan)
-        bfeats.append(cc.cc_batch_features(plan))
-        out = torch.empty(int(vo[-1]), dtype=torch.int32, device="cuda")
-        bsweeps.append(batch_sweeps(plan, out))
         cc.cc_batch_free(plan)
-        del out
         for g in range(cnt):
             a, b = int(eo[g]), int(eo[g + 1])
             t = time_schedules(int(vo[g + 1] - vo[g]), s[a:b], d[a:b])
@@ -114,18 +152,31 @@ def build_training_set(n_graphs, chunk, log):
         torch.cuda.empty_cache()
         log(f"training graphs: {done}/{n_graphs}")
     T = np.array(all_times)
-    Sw = np.concatenate(bsweeps)
-    return (np.array(feats, np.float32), label_times(T), T, np.concatenate(bfeats).astype(np.float32),
-            label_batch(Sw, T), Sw)
+    return np.array(feats, np.float32), label_times(T), T
 
 
-def label_batch(Sw, T):
-    """Batch label: the schedule with the fewest sweeps inside the batch (a
-    round lasts as long as its slowest graph); ties go to the schedule whose
-    single-graph solve was faster."""
-    cand = np.array(BATCH_CLASSES)
-    key = Sw.astype(np.float64) * 1e6 + T[:, cand] / T[:, cand].max(axis=1, keepdims=True)
-    return cand[np.argmin(key, axis=1)].astype(np.int32)
+def train_batch_model(args, log):
+    """The batch model: trained on label_batch labels; returns (blob, report)."""
+    Xb, Sw, ms, swm = build_batch_set(args.train, args.chunk, log)
+    yb, cost = label_batch(Sw, ms, swm)
+    idx = np.arange(len(yb))
+    val = idx % 10 == 0
+    blob_b, loss_b = cc.cc_sched_train(Xb[~val], yb[~val], epochs=args.epochs, batch=256, lr=2e-3, seed=8)
+    cc.cc_sched_load_batch(blob_b)
+    pred_b, _ = cc.cc_sched_predict_batch(Xb[val])
+    val_acc_b = float((pred_b == yb[val]).mean())
+    col = {k: i for i, k in enumerate(BATCH_CLASSES)}
+    key = Sw[val] * cost[None, :]
+    chosen = key[np.arange(val.sum()), [col.get(int(k), 2) for k in pred_b]]
+    cost_ratio_b = float(chosen.sum() / key.min(axis=1).sum())
+    blob_b, loss_b = cc.cc_sched_train(Xb, yb, epochs=args.epochs, batch=256, lr=2e-3, seed=8)
+    cc.cc_sched_load_batch(blob_b)
+    with open(args.out_batch, "wb") as f:
+        f.write(blob_b)
+    log(f"batch model: loss {loss_b:.4f}, validation accuracy {val_acc_b:.3f}, est. cost vs best {cost_ratio_b:.3f}")
+    return {"label_histogram": np.bincount(yb, minlength=cc.CC_SCHED_CLASSES).tolist(),
+            "cost_per_swept_edge_ms": cost.tolist(), "final_loss": loss_b,
+            "validation_accuracy": val_acc_b, "validation_est_cost_ratio_to_best": cost_ratio_b}
 
 
 def evaluate_batch(n_mix, log, reps=3):
@@ -231,6 +282,8 @@ def main():
     ap.add_argument("--out-batch", default=os.path.join(HERE, "sched_weights_batch.bin"))
     ap.add_argument("--report", default=os.path.join(os.path.dirname(HERE), "profiles", "sched_weights.json"))
     ap.add_argument("--dump", default="", help="also save features, labels and timings (.npz)")
+    ap.add_argument("--batch-only", action="store_true",
+                    help="train only the batch model (the single-graph weights in --out stay)")
     ap.add_argument("--eval-only", action="store_true",
                     help="evaluate the weights in --out on the held-out set and update the report")
     args = ap.parse_args()
@@ -256,9 +309,19 @@ def main():
             json.dump(report, f, indent=0, separators=(",", ":"))
         log(f"updated {args.report}")
         return
-    X, y, T, Xb, yb, Sw = build_training_set(args.train, args.chunk, log)
+    if args.batch_only:
+        cc.load_default_scheduler(args.out, None)
+        report = json.load(open(args.report)) if os.path.exists(args.report) else {}
+        bm = train_batch_model(args, log)
+        bm["heldout_batch_ms"] = evaluate_batch(args.heldout, log)
+        report["batch_model"] = bm
+        with open(args.report, "w") as f:
+            json.dump(report, f, indent=0, separators=(",", ":"))
+        log(f"wrote {args.out_batch} and {args.report}")
+        return
+    X, y, T = build_training_set(args.train, args.chunk, log)
     if args.dump:
-        np.savez_compressed(args.dump, X=X, y=y, T=T, Xb=Xb, yb=yb, Sw=Sw)
+        np.savez_compressed(args.dump, X=X, y=y, T=T)
     # 90/10 split for a validation accuracy; the final model trains on all rows
     idx = np.arange(len(y))
     val = idx % 10 == 0
@@ -273,20 +336,8 @@ def main():
     log(f"trained: loss {loss:.4f}, validation accuracy {val_acc:.3f}, mean time ratio to best {regret:.3f}")
     with open(args.out, "wb") as f:
         f.write(blob)
-    # the batch model: same features (after cc_batch_reorder), batch labels
-    blob_b, loss_b = cc.cc_sched_train(Xb[~val], yb[~val], epochs=args.epochs, batch=256, lr=2e-3, seed=8)
-    cc.cc_sched_load_batch(blob_b)
-    pred_b, _ = cc.cc_sched_predict_batch(Xb[val])
-    val_acc_b = float((pred_b == yb[val]).mean())
-    col = {k: i for i, k in enumerate(BATCH_CLASSES)}
-    Swv = Sw[val]
-    sweeps_ratio_b = float(Swv[np.arange(val.sum()), [col.get(int(k), 2) for k in pred_b]].sum() / Swv.min(axis=1).sum())
-    blob_b, loss_b = cc.cc_sched_train(Xb, yb, epochs=args.epochs, batch=256, lr=2e-3, seed=8)
-    cc.cc_sched_load_batch(blob_b)
-    with open(args.out_batch, "wb") as f:
-        f.write(blob_b)
-    log(f"batch model: loss {loss_b:.4f}, validation accuracy {val_acc_b:.3f}, sweeps vs fewest {sweeps_ratio_b:.3f}")
-    batch_eval = evaluate_batch(args.heldout, log)
+    bm = train_batch_model(args, log)
+    bm["heldout_batch_ms"] = evaluate_batch(args.heldout, log)
     rows, tot = evaluate(args.heldout, log)
     label_hist = np.bincount(y, minlength=cc.CC_SCHED_CLASSES).tolist()
     report = {"train_graphs": int(len(y)), "label_histogram": label_hist, "final_loss": loss,
@@ -297,10 +348,7 @@ def main():
               "heldout_first_call_speedup_vs_plain": tot["plain_first_ms"] / tot["learned_first_ms"],
               "heldout_first_call_speedup_vs_c2": tot["c2_first_ms"] / tot["learned_first_ms"],
               "heldout_all_identical": all(r["identical"] for r in rows),
-              "batch_model": {"label_histogram": np.bincount(yb, minlength=cc.CC_SCHED_CLASSES).tolist(),
-                              "final_loss": loss_b, "validation_accuracy": val_acc_b,
-                              "validation_sweeps_ratio_to_fewest": sweeps_ratio_b,
-                              "heldout_batch_ms": batch_eval},
+              "batch_model": bm,
               "heldout": rows}
     with open(args.report, "w") as f:
         json.dump(report, f, indent=0, separators=(",", ":"))
