@@ -464,6 +464,8 @@ def run_ours(args, rank, world, local):
         line["variants"] = variants(cc, g, out, n, m, args, dev, seed, stream, s, d)
     cc.cc_free(g)
     del out
+    if rank == 0 and world == 1 and not args.no_config3 and args.workload.startswith("rmat"):
+        line["config1"] = config1(cc, dev, stream, with_oracle=cpu_leg)
     cc.cc_release_memory()  # the handles' pooled memory goes back before the larger graphs
     if rank == 0 and world == 1 and not args.no_config3 and args.workload.startswith("rmat"):
         del s, d
@@ -599,6 +601,39 @@ def variants(cc, g, out, n, m, args, dev, seed, stream, s=None, d=None):
     return res
 
 
+def config1(cc, dev, stream, with_oracle):
+    """The plain form of config 1: 64 components of 1,024 vertices (32 paths,
+    32 ER with a spanning path), order 2, synchronous, check every sweep, on
+    the edges as generated and after each layout step.  Its labels are
+    compared with union-find and its sweep count with the Alg. 1 simulator
+    (both on the host, a fraction of a second at this size).  The labels
+    (256 KB) and edges (2.4 MB) fit in L2 and a solve takes 13 sweeps of a
+    few microseconds each, so the time is launch and latency, not HBM."""
+    n, s, d = gg.components64(device="cpu")
+    sd, dd = s.to(dev), d.to(dev)
+    res = {"graph": "components64", "n": n, "m": int(s.numel())}
+    want = it = None
+    if with_oracle:
+        import oracle
+        want = oracle.uf_labels(n, s, d)
+        _, it, _, _ = oracle.contour_sync(n, s, d, 2)
+        res["simulator_sweeps"] = it
+    peak, _ = _peaks()
+    out = torch.empty(n, dtype=torch.int32, device=dev)
+    for layout in ("none", "lowdeg", "hub", "degree"):
+        g = cc.cc_init(n, sd, dd, stream=stream.cuda_stream)
+        if layout != "none":
+            cc.cc_graph_reorder(g, REORDER(cc)[layout])
+        r = measure_solves(cc, g, out, int(s.numel()), 2, cc.CC_SYNC, 1, stream, reps=5)
+        if want is not None:
+            r["labels_match_oracle"] = bool(np.array_equal(out.cpu().numpy(), want))
+            if layout != "degree":  # renumbered ids take their own sequence of states (reading 20)
+                r["sweeps_match_simulator"] = r["sweeps"] == it
+        res[f"o2-sync/{layout}"] = r
+        cc.cc_free(g)
+    return res
+
+
 def config3(cc, args, dev, stream, with_oracle):
     """The two largest single graphs: R-MAT scale 27 (2^31 edges, so 64-bit
     edge indices; labels 537 MB, larger than L2) and the caterpillar (2^24
@@ -718,12 +753,24 @@ def batch_compare(cc, G, args, dev, stream, seed):
         return e0.elapsed_time(e1) / reps
 
     reps = max(1, min(args.steps, 5))
+    peak, _ = _peaks()
+    nv, me = np.diff(vo).astype(np.float64), np.diff(eo).astype(np.float64)
+
+    def batch_frac(sweeps, ms, sync):
+        # algorithmic bytes of every graph's sweeps (sync: plus L_u and the copy)
+        per = 8 * me + 4 * nv + (12 * nv if sync else 0)
+        alg = float((np.asarray(sweeps, np.float64) * per).sum())
+        return alg, alg / (ms * 1e-3) / 1e9 / peak
+
     for name, (order, md, c) in [("batched-plain-o2-sync", (2, cc.CC_SYNC, 1)),
                                  ("batched-c2-async", (2, cc.CC_ASYNC, 1)),
                                  ("batched-full-async", (0, cc.CC_ASYNC, 1))]:
         first = ev_ms(lambda: cc.cc_batch_run(plan, out_b, order, md, c), 1)
         ms = ev_ms(lambda: cc.cc_batch_run(plan, out_b, order, md, c), reps)
-        res[name] = {"ms": ms, "first_call_ms": first, "edges_per_s": total_m / (ms * 1e-3)}
+        sw = cc.cc_batch_run(plan, out_b, order, md, c)[0]
+        alg, frac = batch_frac(sw, ms, md == cc.CC_SYNC)
+        res[name] = {"ms": ms, "first_call_ms": first, "edges_per_s": total_m / (ms * 1e-3),
+                     "alg_bytes": alg, "roofline_frac": frac}
     ref = out_b.clone()
     learned = os.path.exists(cc.SCHED_WEIGHTS_PATH)
     per_kind = None
@@ -739,8 +786,11 @@ def batch_compare(cc, G, args, dev, stream, seed):
                         "in_shared_memory": int(((kinds == k) & (ns * 4 <= budget)).sum()),
                         "sweeps_mean": float(sweeps[kinds == k].mean()), "sweeps_max": int(sweeps[kinds == k].max())}
                     for k in sorted(set(kinds.tolist()))}
+        alg, frac = batch_frac(sweeps, ms, False)
         res["batched-learned"] = {"ms": ms, "first_call_ms": first, "edges_per_s": total_m / (ms * 1e-3),
-                                  "note": "first call includes the feature pass and inference"}
+                                  "alg_bytes": alg, "roofline_frac": frac,
+                                  "note": "first call includes the feature pass and inference; bytes counted "
+                                          "as asynchronous sweeps (the batch model picks asynchronous orders)"}
         identical_learned = bool(torch.equal(out_b, ref))
         cc.unload_scheduler()
     handles = []
