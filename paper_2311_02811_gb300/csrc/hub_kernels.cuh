@@ -34,10 +34,29 @@ constexpr int kHubThreads = 1024;   // one block per SM
 constexpr int kHubMax = 24576;      // table entries: one label each -> 96 KB
 constexpr int kHubMinDegree = 16;   // vertices of lower degree are not worth a slot
 
+// The block's view of the hubs: their labels in shared memory (lab[0..K)),
+// their ids in global memory.
+struct HubTab {
+    int32_t* lab;
+    const int32_t* id;
+};
+
+// x <- z for hub `slot` after a read saw its label above z.  Synchronous
+// sweeps write L_u (tested at L2 first, see wr); asynchronous ones write L
+// and lower the block's copy with it.  (A second table collecting the
+// block's L_u minima for the hubs, as the renumbered layout keeps, made the
+// synchronous sweeps of this layout slower: R-MAT 24 7.0 -> 9.1 ms, with the
+// label table cut to half the hubs to make room.)
+template <bool SYNC>
+__device__ __forceinline__ void hub_write(int32_t* L, int32_t* Lu, const HubTab& T, int slot, int32_t z) {
+    wr<SYNC>(L, Lu, T.id[slot], z);
+    if constexpr (!SYNC) atomicMin(T.lab + slot, z);  // the block's copy follows L
+}
+
 // MM^h (h = H) on K edges whose v side may be a hub slot (see mm_fixed).
 template <int H, bool SYNC, int K>
 __device__ __forceinline__ bool mm_fixed_hub(const int32_t (&w)[K], const int32_t (&venc)[K], int32_t* L,
-                                             int32_t* Lu, int32_t* hubL, const int32_t* hubId) {
+                                             int32_t* Lu, const HubTab& T) {
     int32_t cw[K][H + 1], cv[K][H + 1];
 #pragma unroll
     for (int k = 0; k < K; ++k) {
@@ -45,7 +64,7 @@ __device__ __forceinline__ bool mm_fixed_hub(const int32_t (&w)[K], const int32_
         cw[k][1] = rd<SYNC>(L, w[k]);
         if (venc[k] < 0) {
             cv[k][0] = -1;  // id read from the global table only if written
-            cv[k][1] = hubL[~venc[k]];
+            cv[k][1] = T.lab[~venc[k]];
         } else {
             cv[k][0] = venc[k];
             cv[k][1] = rd<SYNC>(L, venc[k]);
@@ -87,10 +106,10 @@ __device__ __forceinline__ bool mm_fixed_hub(const int32_t (&w)[K], const int32_
 #pragma unroll
     for (int k = 0; k < K; ++k) {
 #pragma unroll
-        for (int j = 0; j < H; ++j)
-            if (cv[k][j + 1] > z[k]) wr<SYNC>(L, Lu, (j == 0 && venc[k] < 0) ? hubId[~venc[k]] : cv[k][j], z[k]);
-        if constexpr (!SYNC) {
-            if (venc[k] < 0 && cv[k][1] > z[k]) atomicMin(hubL + ~venc[k], z[k]);
+        for (int j = 0; j < H; ++j) {
+            if (cv[k][j + 1] <= z[k]) continue;
+            if (j == 0 && venc[k] < 0) hub_write<SYNC>(L, Lu, T, ~venc[k], z[k]);
+            else wr<SYNC>(L, Lu, cv[k][j], z[k]);
         }
     }
     return viol;
@@ -100,7 +119,7 @@ __device__ __forceinline__ bool mm_fixed_hub(const int32_t (&w)[K], const int32_
 // a hub's chain comes from the table.
 template <bool SYNC, int K>
 __device__ __forceinline__ bool mm_runtime_hub(const int32_t (&w)[K], const int32_t (&venc)[K], int h, int32_t* L,
-                                               int32_t* Lu, int32_t* hubL, const int32_t* hubId) {
+                                               int32_t* Lu, const HubTab& T) {
     int32_t cur[2 * K], first[2 * K], x[2 * K];
     unsigned act = 0;
 #pragma unroll
@@ -109,7 +128,7 @@ __device__ __forceinline__ bool mm_runtime_hub(const int32_t (&w)[K], const int3
         first[2 * k] = rd<SYNC>(L, w[k]);
         if (venc[k] < 0) {
             x[2 * k + 1] = -1;  // id read from the global table only if written
-            first[2 * k + 1] = hubL[~venc[k]];
+            first[2 * k + 1] = T.lab[~venc[k]];
         } else {
             x[2 * k + 1] = venc[k];
             first[2 * k + 1] = rd<SYNC>(L, venc[k]);
@@ -137,10 +156,10 @@ __device__ __forceinline__ bool mm_runtime_hub(const int32_t (&w)[K], const int3
         z[k] = cur[2 * k] < cur[2 * k + 1] ? cur[2 * k] : cur[2 * k + 1];
         if (first[2 * k] > z[k]) wact |= 1u << (2 * k);
         if (first[2 * k + 1] > z[k]) {
-            if (venc[k] < 0) x[2 * k + 1] = hubId[~venc[k]];
+            if (venc[k] < 0) x[2 * k + 1] = T.id[~venc[k]];
             wact |= 1u << (2 * k + 1);
             if constexpr (!SYNC) {
-                if (venc[k] < 0) atomicMin(hubL + ~venc[k], z[k]);
+                if (venc[k] < 0) atomicMin(T.lab + ~venc[k], z[k]);
             }
         }
     }
@@ -174,9 +193,8 @@ mm_sweep_hub_kernel(const int32_t* __restrict__ src, const int32_t* __restrict__
                     const int32_t* __restrict__ hubs, int K) {
     if (gate != 0 && ctl->sched_h != gate) return;
     extern __shared__ int32_t hub_smem[];
-    int32_t* hubL = hub_smem;
-    const int32_t* hubId = hubs;  // ids stay in global memory
-    for (int i = threadIdx.x; i < K; i += blockDim.x) hubL[i] = rd<SYNC>(L, hubs[i]);
+    const HubTab T{hub_smem, hubs};  // ids stay in global memory
+    for (int i = threadIdx.x; i < K; i += blockDim.x) hub_smem[i] = rd<SYNC>(L, hubs[i]);
     __syncthreads();
     const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -190,12 +208,12 @@ mm_sweep_hub_kernel(const int32_t* __restrict__ src, const int32_t* __restrict__
             load4(src + g * 4, w);
             load4(dst + g * 4, v);
 #pragma unroll
-            for (int k = 0; k < 4; ++k) viol |= identity_pair(w[k], v[k] < 0 ? hubId[~v[k]] : v[k], target);
+            for (int k = 0; k < 4; ++k) viol |= identity_pair(w[k], v[k] < 0 ? T.id[~v[k]] : v[k], target);
         }
         const int64_t t = q4 * 4 + tid;
         if (t < m) {
             const int32_t v = __ldcs(dst + t);
-            viol |= identity_pair(__ldcs(src + t), v < 0 ? hubId[~v] : v, target);
+            viol |= identity_pair(__ldcs(src + t), v < 0 ? T.id[~v] : v, target);
         }
     } else {
         // The next group's edges are loaded before this group's gathers, so
@@ -218,15 +236,15 @@ mm_sweep_hub_kernel(const int32_t* __restrict__ src, const int32_t* __restrict__
                 load4(src + gn * 4, wn);
                 load4(dst + gn * 4, vn);
             }
-            if constexpr (H > 0) viol |= mm_fixed_hub<H, SYNC, 4>(w, v, L, Lu, hubL, hubId);
-            else viol |= mm_runtime_hub<SYNC, 4>(w, v, h, L, Lu, hubL, hubId);
+            if constexpr (H > 0) viol |= mm_fixed_hub<H, SYNC, 4>(w, v, L, Lu, T);
+            else viol |= mm_runtime_hub<SYNC, 4>(w, v, h, L, Lu, T);
         }
         const int64_t t = q4 * 4 + tid;
         if (t < m) {
             int32_t w[1] = {__ldcs(src + t)};
             int32_t v[1] = {__ldcs(dst + t)};
-            if constexpr (H > 0) viol |= mm_fixed_hub<H, SYNC, 1>(w, v, L, Lu, hubL, hubId);
-            else viol |= mm_runtime_hub<SYNC, 1>(w, v, h, L, Lu, hubL, hubId);
+            if constexpr (H > 0) viol |= mm_fixed_hub<H, SYNC, 1>(w, v, L, Lu, T);
+            else viol |= mm_runtime_hub<SYNC, 1>(w, v, h, L, Lu, T);
         }
     }
     if (flag != nullptr) {
