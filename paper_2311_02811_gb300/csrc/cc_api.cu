@@ -661,6 +661,12 @@ static cudaError_t enqueue_init(cc_graph* g, IdT* L, IdT* Lu, const void* init, 
     return cudaGetLastError();
 }
 
+// a[i] = v for i < n
+static __global__ void fill_i32_kernel(int32_t* a, int64_t n, int32_t v) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) a[i] = v;
+}
+
 // Label mapping of a renumbered handle (relabel_kernels.cuh): every tree of
 // src gets the smallest key[] of its members, and out[x] = that minimum for
 // the tree of map[x].  Export: src = the new-id labels, key = inv, map = perm;
@@ -670,7 +676,9 @@ static cudaError_t enqueue_init(cc_graph* g, IdT* L, IdT* Lu, const void* init, 
 static cudaError_t enqueue_map(cc_graph* g, const int32_t* src, const int32_t* key, const int32_t* map,
                                int32_t* out, cudaStream_t s, bool stars_if_converged) {
     const Ctl* ctl = stars_if_converged ? g->ctl : nullptr;
-    cudaError_t e = cudaMemsetAsync(g->tree_min, 0x7f, (size_t)g->n * sizeof(int32_t), s);  // > every id
+    auto kf = fill_i32_kernel;
+    kf<<<grid_for(kf, g->n), kThreads, 0, s>>>(g->tree_min, g->n, 0x7fffffff);  // above every id
+    cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     auto kt = cc::tree_min_kernel;
     kt<<<grid_for(kt, g->n / 64 + 1), kThreads, 0, s>>>(src, key, g->n, g->tree_min, ctl, &g->ctl->bad_count);
