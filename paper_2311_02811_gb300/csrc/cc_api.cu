@@ -309,7 +309,12 @@ static cudaError_t launch_sweep_m(const cc_graph* g, int order, IdT* L, IdT* Lu,
     switch (order) {
         case 1: return launch_sweep_t<1, SYNC, IdT>(g, L, Lu, 1, flag, first, s);
         case 2: return launch_sweep_t<2, SYNC, IdT>(g, L, Lu, 2, flag, first, s);
-        case 4: return launch_sweep_t<4, SYNC, IdT>(g, L, Lu, 4, flag, first, s);
+        // order 4 runs on the run-time-order kernels: their chains advance
+        // in lockstep and stop at roots, and they fit each layout's register
+        // budget, where four unrolled order-4 chains per thread spill or
+        // halve the resident warps (R-MAT 24, hub layout, asynchronous:
+        // 4.03 -> 2.31 ms per solve; grid 4096²: 1.50 -> 1.28 ms)
+        case 4: return launch_sweep_t<0, SYNC, IdT>(g, L, Lu, 4, flag, first, s);
         case CC_ORDER_FULL: return launch_sweep_t<0, SYNC, IdT>(g, L, Lu, cc::kFullChainHops, flag, first, s);
         default: return launch_sweep_t<0, SYNC, IdT>(g, L, Lu, order, flag, first, s);
     }
