@@ -443,7 +443,7 @@ def run_ours(args, rank, world, local):
                 "entry": args.entry,
                 "edge_order": ("as generated (shuffled)" if not reorder else
                                f"cc_graph_reorder({args.reorder}) once before timing, "
-                               f"{reorder_ms:.1f} ms host-timed; inside the e2e timing"),
+                               f"{reorder_ms:.1f} ms host-timed; inside e2e_handle_reorder's timing"),
                 "sweeps_per_step": statistics.median(sweeps)},
         "roofline": {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak,
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
@@ -456,9 +456,13 @@ def run_ours(args, rank, world, local):
     }
 
     if not args.no_e2e:
-        line["e2e"] = e2e(cc, n, s, d, args, mode, world, stream, reorder)
+        # the one-shot call a user with host edges makes, then the handle
+        # pipelines (upload, [the timed handle's layout step], solve) for context
+        line["e2e"] = e2e(cc, n, s, d, args, mode, world, stream, 0, "solve_host")
+        line["e2e_handle"] = e2e(cc, n, s, d, args, mode, world, stream, 0, "handle")
         if reorder:
-            line["e2e_without_reorder"] = e2e(cc, n, s, d, args, mode, world, stream, 0)
+            line["e2e_handle_reorder"] = e2e(cc, n, s, d, args, mode, world, stream, reorder, "handle")
+        e2e_labels = [line[k].pop("labels") for k in ("e2e", "e2e_handle", "e2e_handle_reorder") if k in line]
 
     if not args.no_variants and rank == 0:
         line["variants"] = variants(cc, g, out, n, m, args, dev, seed, stream, s, d)
@@ -481,6 +485,8 @@ def run_ours(args, rank, world, local):
     if cpu_leg:
         want, dt = job.get()
         line["labels_match_oracle"] = bool(np.array_equal(timed_labels, want))
+        if not args.no_e2e:
+            line["e2e_labels_match_oracle"] = all(bool(np.array_equal(x, want)) for x in e2e_labels)
         line["cpu_baseline"] = {"value": m / dt, "unit": "edges/s", "cores": 1, "kind": "oracle",
                                 "sample": f"serial union-find over all {m:,} edges and {n:,} vertices "
                                           f"of the timed graph, {dt:.1f} s; its labels are compared "
@@ -490,14 +496,21 @@ def run_ours(args, rank, world, local):
         print(json.dumps(line), flush=True)
 
 
-def e2e(cc, n, s, d, args, mode, world, stream, reorder=0):
-    """Same metric through the public API from pinned host buffers, copies included."""
+def e2e(cc, n, s, d, args, mode, world, stream, reorder=0, pipeline="solve_host"):
+    """Same metric through the public API from pinned host buffers, copies
+    included.  pipeline "solve_host": one cc_solve_host call (the upload
+    overlapped with sweeps); "handle": cc_init (upload) + [cc_graph_reorder] +
+    cc_run + cc_free.  Labels come back to pinned host memory."""
     s_h = s.cpu().pin_memory()
     d_h = d.cpu().pin_memory()
     out_h = torch.empty(n, dtype=torch.int32).pin_memory()
     m = s_h.numel()
 
     def one():
+        if pipeline == "solve_host":
+            cc.cc_solve_host(n, s_h, d_h, out_h, args.order, mode, args.interval, out_on_device=False,
+                             stream=stream.cuda_stream)
+            return
         g = cc.cc_init(n, s_h, d_h, on_device=False, stream=stream.cuda_stream)
         if reorder:
             cc.cc_graph_reorder(g, reorder)
@@ -517,9 +530,11 @@ def e2e(cc, n, s, d, args, mode, world, stream, reorder=0):
     ev1.record(stream)
     torch.cuda.synchronize()
     ms = max_over_ranks(ev0.elapsed_time(ev1), world)
+    call = ("cc_solve_host" if pipeline == "solve_host" else
+            "cc_init + " + ("cc_graph_reorder + " if reorder else "") + "cc_run + cc_free")
     return {"value": m * steps * world / (ms * 1e-3), "unit": "edges/s",
             "h2d_bytes_per_step": 2 * 4 * m, "d2h_bytes_per_step": 4 * n, "steps": steps,
-            "ms_per_step": ms / steps}
+            "ms_per_step": ms / steps, "call": call, "labels": out_h.numpy().copy()}
 
 
 def measure_solves(cc, gh, o, mm, order, mode, c, stream, reps=3):

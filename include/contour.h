@@ -174,6 +174,45 @@ cc_status cc_run(cc_graph *g, int order, int mode, int check_interval, int32_t m
                  const void *init_labels, void *labels_out, int out_on_device, cc_stats *stats);
 
 /*
+ * cc_solve_host -- one solve of an edge list held in HOST memory: cc_init,
+ * cc_run and cc_free in one call, with the upload overlapped with sweeps.
+ *
+ * The edges cross the host link in chunks of 2^24 edges on a copy stream of
+ * their own.  Each chunk is checked (ids in [0, n)) as soon as it has landed,
+ * and in CC_ASYNC mode the order-h operator of Def. 3 is applied once to each
+ * of its edges, in place, while the later chunks are still in flight: in the
+ * asynchronous iteration (Section III-B1) an edge may be applied at any time,
+ * so sweeping the landed part early is one more legal order of applications.
+ * That streamed pass counts as the first sweep.  Once the whole list is
+ * resident the solve continues exactly as cc_run on a handle of the same
+ * edges, from the streamed labels: checked sweeps (Section III-B2) to the
+ * fixed point, then the compress.  CC_SYNC solves only check the chunks in
+ * flight and then run Alg. 1 from L[i] = i, so every synchronous sweep equals
+ * cc_run's.  Labels equal cc_run's in both modes (the unique result of the
+ * fixed point).
+ *
+ *   n, src, dst, m  int32 COO edges in host memory (pinned memory lets the
+ *                   copies run asynchronously and overlap; pageable memory
+ *                   works, without overlap).  Read only; not kept.
+ *   order           h >= 1 or CC_ORDER_FULL (no CC_ORDER_AUTO or schedules).
+ *   mode            CC_SYNC or CC_ASYNC.
+ *   check_interval, max_sweeps, labels_out, out_on_device  as for cc_run
+ *                   (CC_ASYNC: max_sweeps >= 2, the streamed pass included).
+ *   stats           as for cc_run; solve_ms covers the whole call on the
+ *                   device from the first copy to the compress, and sweeps
+ *                   and alg_bytes include the streamed pass.
+ *   cuda_stream     the stream the sweeps run on (synchronised before
+ *                   returning); the copies use a stream of their own.
+ * Errors: CC_EIDRANGE if an id lies outside [0, n) (such an edge is never
+ * used by a gather), otherwise as for cc_init and cc_run.  Device memory
+ * comes from the library's stream-ordered pool and is returned before the
+ * call returns.
+ */
+cc_status cc_solve_host(int64_t n, const int32_t *src, const int32_t *dst, int64_t m, int order, int mode,
+                        int check_interval, int32_t max_sweeps, void *labels_out, int out_on_device,
+                        cc_stats *stats, void *cuda_stream);
+
+/*
  * cc_run_noalloc -- the same computation as cc_run, for callers that cannot
  * allocate device memory.  The paper has no counterpart to this entry point.
  *

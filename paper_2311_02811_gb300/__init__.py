@@ -19,7 +19,7 @@ __all__ = [
     "CC_ETIMEOUT", "CC_ID32", "CC_ID64", "CC_COO", "CC_CSR", "CC_CSR_NATIVE", "CC_CSR_NATIVE_SYM",
     "CC_SYNC", "CC_ASYNC", "CC_ASYNC_COMPACT",
     "CC_ORDER_FULL", "CC_ORDER_AUTO", "CC_ORDER_11MM", "CC_ORDER_1M1M", "CC_NOALLOC_MAX_N", "CCError", "cc_stats", "cc_graph", "lib", "LIB_PATH",
-    "cc_init", "cc_run", "cc_run_noalloc", "cc_free", "cc_release_memory", "cc_batch_plan", "cc_batch_init",
+    "cc_init", "cc_run", "cc_solve_host", "cc_run_noalloc", "cc_free", "cc_release_memory", "cc_batch_plan", "cc_batch_init",
     "cc_batch_run", "cc_batch_set_schedule", "cc_batch_run_scheduled", "cc_batch_tuning",
     "cc_batch_set_tuning", "cc_batch_reorder", "cc_batch_edges", "cc_batch_free", "cc_batch", "cc_sched_load", "cc_sched_blob_bytes",
     "cc_sched_param_count", "cc_sched_decode", "cc_graph_features", "cc_batch_features",
@@ -69,6 +69,9 @@ lib.cc_run.argtypes = [_p, _int, _int, _int, _i32, _p, _p, _int, ctypes.POINTER(
 lib.cc_run.restype = _int
 lib.cc_run_noalloc.argtypes = [_i64, _p, _p, _i64, _int, _int, _int, _i32, _p,
                                ctypes.POINTER(_i32), _p]
+lib.cc_solve_host.argtypes = [_i64, _p, _p, _i64, _int, _int, _int, _i32, _p, _int,
+                              ctypes.POINTER(cc_stats), _p]
+lib.cc_solve_host.restype = _int
 lib.cc_run_noalloc.restype = _int
 lib.cc_graph_info.argtypes = [_p, ctypes.POINTER(_i64), ctypes.POINTER(_i64)]
 lib.cc_graph_info.restype = _int
@@ -171,6 +174,31 @@ def cc_run(g, labels_out, order=2, mode=CC_ASYNC, check_interval=1, max_sweeps=1
                     int(bool(out_on_device)), ctypes.byref(st))
     if raise_on_error:
         _check(rc, "cc_run", st)
+        return st
+    return rc, st
+
+
+def cc_solve_host(n, src, dst, labels_out, order=2, mode=CC_ASYNC, check_interval=1, max_sweeps=1 << 20,
+                  out_on_device=None, stream=None, raise_on_error=True):
+    """One solve of int32 edges held in host memory, the upload overlapped with
+    sweeps (cc_solve_host in contour.h); returns cc_stats."""
+    def host_i32(x, what):
+        if hasattr(x, "data_ptr") and x.device.type != "cpu":
+            raise ValueError(f"cc_solve_host: {what} must be host memory (use cc_init + cc_run for device edges)")
+        if "int32" not in str(getattr(x, "dtype", "")):
+            raise ValueError(f"cc_solve_host: {what} must be int32")
+        return _ptr(x)[0]
+
+    ps = host_i32(src, "src")
+    pd = host_i32(dst, "dst")
+    po, do = _ptr(labels_out)
+    if out_on_device is None:
+        out_on_device = do
+    st = cc_stats()
+    rc = lib.cc_solve_host(int(n), ps, pd, len(src), int(order), int(mode), int(check_interval),
+                           int(max_sweeps), po, int(bool(out_on_device)), ctypes.byref(st), _stream(stream))
+    if raise_on_error:
+        _check(rc, "cc_solve_host", st)
         return st
     return rc, st
 

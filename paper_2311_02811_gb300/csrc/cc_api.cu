@@ -26,6 +26,7 @@
 #include "hub_kernels.cuh"
 #include "compact_kernels.cuh"
 #include "relabel_kernels.cuh"
+#include "stream_kernels.cuh"
 
 using cc::Ctl;
 
@@ -596,6 +597,32 @@ static cc_status init_edges(cc_graph* g, int layout, const void* a, const void* 
     return CC_OK;
 }
 
+// A handle without edges: control block, events, capture stream.
+static cc_status new_handle(int64_t n, int id_bits, cudaStream_t s, const char* who, cc_graph** out) {
+    cc_graph* g = new (std::nothrow) cc_graph();
+    if (!g) return set_error(CC_ENOMEM, "%s: host allocation failed", who);
+    g->n = n;
+    g->id_bits = id_bits;
+    g->stream = s;
+    cudaError_t e = cc::dmalloc(reinterpret_cast<void**>(&g->ctl), sizeof(Ctl), s);
+    if (e == cudaSuccess) e = cudaMallocHost(&g->ctl_h, sizeof(Ctl));
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&g->cap, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreate(&g->ev0);
+    if (e == cudaSuccess) e = cudaEventCreate(&g->ev1);
+    if (e == cudaSuccess) e = cudaEventCreate(&g->evl0);
+    if (e == cudaSuccess) e = cudaEventCreate(&g->evl1);
+    if (e == cudaSuccess) {
+        cc::ctl_reset_kernel<<<1, 32, 0, s>>>(g->ctl, 1, 0);
+        e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) {
+        destroy(g);
+        return cuda_fail(e, who, __FILE__, __LINE__);
+    }
+    *out = g;
+    return CC_OK;
+}
+
 extern "C" cc_status cc_init(cc_graph** out, int64_t n, int id_bits, int layout, const void* a,
                              const void* b, int64_t cnt, int on_device, void* cuda_stream) {
     cc::NvtxRange range("cc_init");
@@ -613,28 +640,13 @@ extern "C" cc_status cc_init(cc_graph** out, int64_t n, int id_bits, int layout,
     if (cnt > 0 && (!a || !b)) return set_error(CC_EINVAL, "cc_init: edge arrays are NULL");
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
 
-    cc_graph* g = new (std::nothrow) cc_graph();
-    if (!g) return set_error(CC_ENOMEM, "cc_init: host allocation failed");
-    g->n = n;
-    g->id_bits = id_bits;
-    g->stream = s;
-    cc_status st = CC_OK;
+    cc_graph* g = nullptr;
+    cc_status st = new_handle(n, id_bits, s, "cc_init", &g);
+    if (st != CC_OK) return st;
     auto fail = [&](cc_status x) {
         destroy(g);
         return x;
     };
-    {
-        cudaError_t e = cc::dmalloc(reinterpret_cast<void**>(&g->ctl), sizeof(Ctl), s);
-        if (e == cudaSuccess) e = cudaMallocHost(&g->ctl_h, sizeof(Ctl));
-        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&g->cap, cudaStreamNonBlocking);
-        if (e == cudaSuccess) e = cudaEventCreate(&g->ev0);
-        if (e == cudaSuccess) e = cudaEventCreate(&g->ev1);
-        if (e == cudaSuccess) e = cudaEventCreate(&g->evl0);
-        if (e == cudaSuccess) e = cudaEventCreate(&g->evl1);
-        if (e != cudaSuccess) return fail(cuda_fail(e, "cc_init allocation", __FILE__, __LINE__));
-    }
-    cc::ctl_reset_kernel<<<1, 32, 0, s>>>(g->ctl, 1, 0);
-    if (cudaGetLastError() != cudaSuccess) return fail(set_error(CC_ECUDA, "cc_init: launch failed"));
     st = native ? init_csr_native(g, layout, a, b, cnt, on_device, s)
          : (id_bits == 64) ? init_edges<int64_t>(g, layout, a, b, cnt, on_device, s)
                            : init_edges<int32_t>(g, layout, a, b, cnt, on_device, s);
@@ -882,6 +894,140 @@ static cc_status run_impl(cc_graph* g, int order, int mode, int c, int32_t max_s
         return set_error(CC_ECUDA, "cc_run: converged state was not a set of stars (%llu labels moved)",
                          h.compress_changes);
     return CC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// cc_solve_host: one solve of a host edge list, the upload overlapped with sweeps
+// ---------------------------------------------------------------------------
+
+constexpr int64_t kStreamChunk = 1ll << 24;  // edges per chunk (64 MB of each id array)
+
+template <int H>
+static cudaError_t launch_chunk(const int32_t* src, const int32_t* dst, int64_t cnt, int64_t base, int64_t n,
+                                int32_t* L, int h, Ctl* ctl, int sweep, cudaStream_t s) {
+    auto k = cc::chunk_sweep_kernel<H>;
+    k<<<grid_for(k, cnt / 4 + 1), kThreads, 0, s>>>(src, dst, cnt, base, n, L, h, ctl, sweep);
+    return cudaGetLastError();
+}
+
+extern "C" cc_status cc_solve_host(int64_t n, const int32_t* src, const int32_t* dst, int64_t m, int order,
+                                   int mode, int c, int32_t max_sweeps, void* labels_out, int out_on_device,
+                                   cc_stats* stats, void* cuda_stream) {
+    cc::NvtxRange range("cc_solve_host");
+    g_last_error.clear();
+    if (n < 0 || m < 0) return set_error(CC_EINVAL, "cc_solve_host: negative n or m");
+    if (n > 0x7fffffffLL) return set_error(CC_EINVAL, "cc_solve_host: int32 ids (n < 2^31)");
+    if (m > 0 && (!src || !dst)) return set_error(CC_EINVAL, "cc_solve_host: edge arrays are NULL");
+    if (n > 0 && !labels_out) return set_error(CC_EINVAL, "cc_solve_host: labels_out is NULL");
+    if (mode != CC_SYNC && mode != CC_ASYNC) return set_error(CC_EINVAL, "cc_solve_host: mode must be CC_SYNC or CC_ASYNC");
+    if (order < 0 || order > CC_MAX_ORDER)
+        return set_error(CC_EINVAL, "cc_solve_host: order must be 1..%d or CC_ORDER_FULL", CC_MAX_ORDER);
+    if (c < 1 || c > 64) return set_error(CC_EINVAL, "cc_solve_host: check_interval must be 1..64");
+    for (const void* p : {static_cast<const void*>(src), static_cast<const void*>(dst)}) {
+        if (m == 0) break;
+        cudaPointerAttributes at;
+        if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+            cudaGetLastError();
+            continue;  // not known to CUDA: pageable host memory
+        }
+        if (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged)
+            return set_error(CC_EINVAL, "cc_solve_host: src and dst must be host memory (device edges: cc_init + cc_run)");
+    }
+    const bool async = mode == CC_ASYNC;
+    // the streamed pass counts as the first sweep of an asynchronous solve
+    if (max_sweeps < (async ? 2 : 1))
+        return set_error(CC_EINVAL, "cc_solve_host: max_sweeps must be >= %d", async ? 2 : 1);
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    cc_graph* g = nullptr;
+    cc_status st = new_handle(n, CC_ID32, s, "cc_solve_host", &g);
+    if (st != CC_OK) return st;
+    cudaStream_t cs = nullptr;  // copy stream
+    std::vector<cudaEvent_t> evs;
+    cudaEvent_t ev_start = nullptr;
+    auto done = [&](cc_status x) {
+        for (cudaEvent_t e : evs) cudaEventDestroy(e);
+        if (ev_start) cudaEventDestroy(ev_start);
+        if (cs) {
+            cudaStreamSynchronize(cs);
+            cudaStreamDestroy(cs);
+        }
+        destroy(g);
+        return x;
+    };
+#define SH_CUDA(expr)                                                              \
+    do {                                                                           \
+        cudaError_t e_ = (expr);                                                   \
+        if (e_ != cudaSuccess) return done(cuda_fail(e_, #expr, __FILE__, __LINE__)); \
+    } while (0)
+    g->m = m;
+    g->own_edges = true;
+    const int64_t K = (m + kStreamChunk - 1) / kStreamChunk;
+    SH_CUDA(cudaEventCreate(&ev_start));
+    SH_CUDA(cudaEventRecord(ev_start, s));
+    SH_CUDA(cc::dmalloc(&g->src, (size_t)(m > 0 ? m : 1) * sizeof(int32_t), s));
+    SH_CUDA(cc::dmalloc(&g->dst, (size_t)(m > 0 ? m : 1) * sizeof(int32_t), s));
+    // the labels the streamed sweeps lower are the ones the loop starts from
+    // (the caller's output when it is an aligned device buffer, as in cc_run)
+    int32_t* L = nullptr;
+    if (async && n > 0) {
+        if (out_on_device && (reinterpret_cast<uintptr_t>(labels_out) & 15) == 0) {
+            L = static_cast<int32_t*>(labels_out);
+        } else {
+            SH_CUDA(cc::dmalloc(&g->L, (size_t)n * sizeof(int32_t), s));
+            L = static_cast<int32_t*>(g->L);
+        }
+        auto ki = cc::iota_kernel<int32_t>;
+        ki<<<grid_for(ki, n), kThreads, 0, s>>>(L, nullptr, n);
+        SH_CUDA(cudaGetLastError());
+    }
+    if (K > 0) {
+        SH_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+        evs.resize((size_t)K + 1, nullptr);
+        for (auto& e : evs) SH_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        // copies start once the edge arrays exist on the compute stream
+        SH_CUDA(cudaEventRecord(evs[K], s));
+        SH_CUDA(cudaStreamWaitEvent(cs, evs[K], 0));
+        int32_t* ds = static_cast<int32_t*>(g->src);
+        int32_t* dd = static_cast<int32_t*>(g->dst);
+        for (int64_t k = 0; k < K; ++k) {
+            const int64_t off = k * kStreamChunk;
+            const int64_t len = std::min<int64_t>(kStreamChunk, m - off);
+            SH_CUDA(cudaMemcpyAsync(ds + off, src + off, (size_t)len * sizeof(int32_t), cudaMemcpyHostToDevice, cs));
+            SH_CUDA(cudaMemcpyAsync(dd + off, dst + off, (size_t)len * sizeof(int32_t), cudaMemcpyHostToDevice, cs));
+            SH_CUDA(cudaEventRecord(evs[k], cs));
+        }
+        // each landed chunk: ids checked, and (asynchronous solves) swept once
+        const int sweep = (async && n > 0) ? 1 : 0;
+        const int h = order == CC_ORDER_FULL ? cc::kFullChainHops : order;
+        for (int64_t k = 0; k < K; ++k) {
+            const int64_t off = k * kStreamChunk;
+            const int64_t len = std::min<int64_t>(kStreamChunk, m - off);
+            SH_CUDA(cudaStreamWaitEvent(s, evs[k], 0));
+            cudaError_t e = order == 1   ? launch_chunk<1>(ds + off, dd + off, len, off, n, L, h, g->ctl, sweep, s)
+                            : order == 2 ? launch_chunk<2>(ds + off, dd + off, len, off, n, L, h, g->ctl, sweep, s)
+                                         : launch_chunk<0>(ds + off, dd + off, len, off, n, L, h, g->ctl, sweep, s);
+            SH_CUDA(e);
+        }
+    }
+    SH_CUDA(cudaMemcpyAsync(g->ctl_h, g->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
+    SH_CUDA(cudaStreamSynchronize(s));
+    if (g->ctl_h->bad_count)
+        return done(set_error(CC_EIDRANGE, "%llu edges with an endpoint outside [0, %lld) (first at edge %llu)",
+                              g->ctl_h->bad_count, (long long)n, g->ctl_h->first_bad));
+    // the ordinary loop of checked sweeps (cc_run), from the streamed labels
+    st = run_impl(g, order, mode, c, async ? max_sweeps - 1 : max_sweeps, L, labels_out, out_on_device, stats, s);
+    if (stats) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, ev_start, g->ev1) == cudaSuccess) stats->solve_ms = ms;
+        else cudaGetLastError();  // the loop stopped before its last event: keep cc_run's time
+        if (async && n > 0 && m > 0) {
+            stats->sweeps += 1;
+            stats->alg_bytes += 8.0 * (double)m + 4.0 * (double)n;
+        }
+        stats->edges_per_s = stats->solve_ms > 0 ? (double)m / (stats->solve_ms * 1e-3) : 0.0;
+    }
+#undef SH_CUDA
+    return done(st);
 }
 
 extern "C" cc_status cc_graph_edges(const cc_graph* g, const void** src, const void** dst) {
