@@ -179,11 +179,16 @@ cc_status cc_run(cc_graph *g, int order, int mode, int check_interval, int32_t m
  *
  * The edges cross the host link in chunks of 2^24 edges on a copy stream of
  * their own.  Each chunk is checked (ids in [0, n)) as soon as it has landed,
- * and in CC_ASYNC mode the order-h operator of Def. 3 is applied once to each
- * of its edges, in place, while the later chunks are still in flight: in the
- * asynchronous iteration (Section III-B1) an edge may be applied at any time,
- * so sweeping the landed part early is one more legal order of applications.
- * That streamed pass counts as the first sweep.  Once the whole list is
+ * stored as (smaller id, larger id) and, on graphs of average degree 8 or more
+ * (m >= 4n), sorted by the smaller id into its place in the edge arrays (the
+ * operator is symmetric in w and v, and edge order never changes the result);
+ * the chunks after the bulk halve in size, so little is left to do once the
+ * last copy lands.  In CC_ASYNC mode the order-h operator
+ * of Def. 3 is applied once to each of its edges, in place, while the later
+ * chunks are still in flight: in the asynchronous iteration (Section III-B1)
+ * an edge may be applied at any time, so sweeping the landed part early is one
+ * more legal order of applications.  That streamed pass counts as the first
+ * sweep.  Once the whole list is
  * resident the solve continues exactly as cc_run on a handle of the same
  * edges, from the streamed labels: checked sweeps (Section III-B2) to the
  * fixed point, then the compress.  CC_SYNC solves only check the chunks in

@@ -55,6 +55,14 @@ bool graph_relabeled(const cc_graph* g);
 cc_status resolve_schedule(cc_graph* g, int* order, int* mode, int* c, bool* deferred);
 cc_status sched_defer_features(cc_graph* g, cudaStream_t s);
 
+// Stable radix sort of cnt (key, value) pairs by the low end_bit bits of the
+// key, between two buffer pairs (reorder.cu): the input in (k0, v0), the
+// other pair as scratch; *in_second says which pair holds the result.  temp ==
+// nullptr: only sets *temp_bytes.
+cudaError_t sort_pairs_u32(void* temp, size_t* temp_bytes, uint32_t* k0, uint32_t* k1, uint32_t* v0, uint32_t* v1,
+                           int64_t cnt, int end_bit, cudaStream_t s, bool* in_second);
+int key_bits(int64_t n);
+
 // Batched path (batch.cu) and its schedule resolution (sched.cu).
 cc_status batch_solve(cc_batch_plan* b, int32_t max_sweeps, int32_t* labels_out, int32_t* sweeps_out,
                       double* solve_ms);

@@ -247,6 +247,20 @@ done:
 
 }  // namespace
 
+namespace cc {
+
+int key_bits(int64_t n) { return bits_for(n); }
+
+cudaError_t sort_pairs_u32(void* temp, size_t* temp_bytes, uint32_t* k0, uint32_t* k1, uint32_t* v0, uint32_t* v1,
+                           int64_t cnt, int end_bit, cudaStream_t s, bool* in_second) {
+    cub::DoubleBuffer<uint32_t> keys(k0, k1), vals(v0, v1);
+    cudaError_t e = cub::DeviceRadixSort::SortPairs(temp, *temp_bytes, keys, vals, (long long)cnt, 0, end_bit, s);
+    if (in_second) *in_second = keys.Current() == k1;
+    return e;
+}
+
+}  // namespace cc
+
 extern "C" cc_status cc_graph_reorder(cc_graph* g, int method) {
     cc::NvtxRange range("cc_graph_reorder");
     if (!g) return cc::set_error(CC_EINVAL, "cc_graph_reorder: g is NULL");

@@ -65,11 +65,12 @@ def test_sync_sweeps_match_simulator(cc, family):
     assert np.array_equal(out.numpy(), want)
 
 
-def test_several_chunks_with_ragged_tail(cc):
-    """m = 2^24 + 2^23 + 3: two chunks of the streamed upload, the second
-    ragged (not a multiple of 4 edges)."""
-    n = 1 << 21
-    m = (1 << 24) + (1 << 23) + 3
+@pytest.mark.parametrize("n,m", [(1 << 21, (1 << 24) + (1 << 23) + 3), (1 << 23, (1 << 24) + (1 << 22) + 1)],
+                         ids=["dense-sorted-chunks", "sparse-chunks-in-place"])
+def test_several_chunks_with_ragged_tail(cc, n, m):
+    """More than 2^24 edges: several chunks of the streamed upload (the tail
+    halving), the last one ragged (not a multiple of 4 edges); average degree
+    12 (chunks sorted) and 2.5 (chunks left in place)."""
     s, d = gg.er(n, m, seed=36)
     want = oracle.uf_labels(n, s, d)
     sp, dp = _pinned(s), _pinned(d)
