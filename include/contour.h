@@ -210,8 +210,9 @@ cc_status cc_run(cc_graph *g, int order, int mode, int check_interval, int32_t m
  *                   returning); the copies use a stream of their own.
  * Errors: CC_EIDRANGE if an id lies outside [0, n) (such an edge is never
  * used by a gather), otherwise as for cc_init and cc_run.  Device memory
- * comes from the library's stream-ordered pool and is returned before the
- * call returns.
+ * (the edge arrays, two staging pairs of 2^24 edges and the sort's scratch
+ * on dense graphs, the labels) comes from the library's stream-ordered pool
+ * and is handed back to it, in stream order, before the call returns.
  */
 cc_status cc_solve_host(int64_t n, const int32_t *src, const int32_t *dst, int64_t m, int order, int mode,
                         int check_interval, int32_t max_sweeps, void *labels_out, int out_on_device,
