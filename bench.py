@@ -479,6 +479,12 @@ def run_ours(args, rank, world, local):
         torch.cuda.empty_cache()
     if args.batch_graphs > 0 and rank == 0:
         line["batch"] = batch_compare(cc, args.batch_graphs, args, dev, stream, gg.BASE_SEED + 3)
+    if rank == 0 and world == 1 and not args.no_config3 and args.workload.startswith("rmat"):
+        # Section IV's delaunay_n10..n24 experiment on the Delaunay-style generator
+        d = delaunay_scaling(cc, args, dev)
+        line["delaunay_scaling"] = {"growth_n10_to_n24": d["growth"],
+                                    "paper_growth_20_core_xeon": d["paper_growth_20_core_xeon"],
+                                    "n24": {k: v for k, v in d["rows"][-1].items()}}
 
     if "config3" in line:
         finish_config3(line["config3"])
@@ -865,11 +871,9 @@ def run_batch(args, rank, world, local):
 PAPER_DELAUNAY_GROWTH = {"C-2": 895, "C-1m1m": 1072, "C-m": 1268, "C-11mm": 1329, "C-Syn": 2705}
 
 
-def run_delaunay_scaling(args, rank):
+def delaunay_scaling(cc, args, dev):
     """Solve time of each Contour variant on Delaunay-style graphs n = 2^10..2^24
     and its growth from n10 to n24 (the paper's delaunay_n10..n24 experiment)."""
-    import paper_2311_02811_gb300 as cc
-    dev = torch.device("cuda", torch.cuda.current_device())
     variants = {"C-Syn": (2, cc.CC_SYNC), "C-1": (1, cc.CC_ASYNC), "C-2": (2, cc.CC_ASYNC),
                 "C-m": (0, cc.CC_ASYNC), "C-11mm": (cc.CC_ORDER_11MM, cc.CC_ASYNC),
                 "C-1m1m": (cc.CC_ORDER_1M1M, cc.CC_ASYNC)}
@@ -890,11 +894,18 @@ def run_delaunay_scaling(args, rank):
         rows.append(row)
         del s, d, out
     growth = {v: rows[-1][v]["ms"] / rows[0][v]["ms"] for v in variants}
+    return {"growth": growth, "paper_growth_20_core_xeon": PAPER_DELAUNAY_GROWTH, "rows": rows}
+
+
+def run_delaunay_scaling(args, rank):
+    import paper_2311_02811_gb300 as cc
+    dev = torch.device("cuda", torch.cuda.current_device())
+    res = delaunay_scaling(cc, args, dev)
     line = {"metric": "Delaunay-style scaling n=2^10..2^24: solve-time growth n10 -> n24",
-            "value": growth["C-2"], "unit": "x", "higher_is_better": False, "n_gpus": 1,
+            "value": res["growth"]["C-2"], "unit": "x", "higher_is_better": False, "n_gpus": 1,
             "data": "synthetic", "dtype": "int32",
             "config": {"workload": "delaunay-like-2^10..2^24", "edges": "jittered grid with Delaunay diagonals"},
-            "growth": growth, "paper_growth_20_core_xeon": PAPER_DELAUNAY_GROWTH, "rows": rows}
+            **res}
     if rank == 0:
         print(json.dumps(line), flush=True)
 
