@@ -191,8 +191,11 @@ cc_status cc_run(cc_graph *g, int order, int mode, int check_interval, int32_t m
  * sweep.  Once the whole list is
  * resident the solve continues exactly as cc_run on a handle of the same
  * edges, from the streamed labels: checked sweeps (Section III-B2) to the
- * fixed point, then the compress.  CC_SYNC solves only check the chunks in
- * flight and then run Alg. 1 from L[i] = i, so every synchronous sweep equals
+ * fixed point, then the compress.  CC_SYNC solves with check_interval 1
+ * stream Alg. 1's first iteration instead, which reads no label (each edge
+ * lowers L_u[max(w, v)] to min(w, v), and these minima commute), and the loop
+ * continues from its result; with a larger interval the chunks are only
+ * checked.  Either way every synchronous state and sweep count equals
  * cc_run's.  Labels equal cc_run's in both modes (the unique result of the
  * fixed point).
  *
@@ -205,7 +208,7 @@ cc_status cc_run(cc_graph *g, int order, int mode, int check_interval, int32_t m
  *                   (CC_ASYNC: max_sweeps >= 2, the streamed pass included).
  *   stats           as for cc_run; solve_ms covers the whole call on the
  *                   device from the first copy to the compress, and sweeps
- *                   and alg_bytes include the streamed pass.
+ *                   and alg_bytes include the streamed pass or iteration.
  *   cuda_stream     the stream the sweeps run on (synchronised before
  *                   returning); the copies use a stream of their own.
  * Errors: CC_EIDRANGE if an id lies outside [0, n) (such an edge is never

@@ -994,9 +994,13 @@ extern "C" cc_status cc_solve_host(int64_t n, const int32_t* src, const int32_t*
     SH_CUDA(cc::dmalloc(&g->src, (size_t)(m > 0 ? m : 1) * sizeof(int32_t), s));
     SH_CUDA(cc::dmalloc(&g->dst, (size_t)(m > 0 ? m : 1) * sizeof(int32_t), s));
     // the labels the streamed sweeps lower are the ones the loop starts from
-    // (the caller's output when it is an aligned device buffer, as in cc_run)
+    // (the caller's output when it is an aligned device buffer, as in cc_run).
+    // Synchronous solves with c = 1 stream Alg. 1's first iteration, which
+    // reads no label: its L_u, built in place from the identity, is the state
+    // the loop continues from.
+    const bool stream_ident = !async && c == 1 && max_sweeps > 1 && n > 0 && m > 0;
     int32_t* L = nullptr;
-    if (async && n > 0) {
+    if ((async || stream_ident) && n > 0) {
         if (out_on_device && (reinterpret_cast<uintptr_t>(labels_out) & 15) == 0) {
             L = static_cast<int32_t*>(labels_out);
         } else {
@@ -1044,6 +1048,7 @@ extern "C" cc_status cc_solve_host(int64_t n, const int32_t* src, const int32_t*
         SH_CUDA(cudaEventRecord(evs[2 * K], s));
         SH_CUDA(cudaStreamWaitEvent(cs, evs[2 * K], 0));
         const int sweep = (async && n > 0) ? 1 : 0;
+        SH_CUDA(cudaMemsetAsync(&g->ctl->flag, 0, sizeof(int32_t), s));
         const int h = order == CC_ORDER_FULL ? cc::kFullChainHops : order;
         for (int64_t k = 0; k < K; ++k) {
             const int64_t off = chunks[k].first;
@@ -1074,6 +1079,10 @@ extern "C" cc_status cc_solve_host(int64_t n, const int32_t* src, const int32_t*
                 SH_CUDA(order == 1   ? launch_chunk<1>(ds + off, dd + off, len, L, h, s)
                         : order == 2 ? launch_chunk<2>(ds + off, dd + off, len, L, h, s)
                                      : launch_chunk<0>(ds + off, dd + off, len, L, h, s));
+            } else if (stream_ident) {
+                auto ki = cc::chunk_identity_kernel;
+                ki<<<grid_for(ki, len / 4 + 1), kThreads, 0, s>>>(ds + off, dd + off, len, L, &g->ctl->flag);
+                SH_CUDA(cudaGetLastError());
             }
         }
     }
@@ -1082,15 +1091,20 @@ extern "C" cc_status cc_solve_host(int64_t n, const int32_t* src, const int32_t*
     if (g->ctl_h->bad_count)
         return done(set_error(CC_EIDRANGE, "%llu edges with an endpoint outside [0, %lld) (first at edge %llu)",
                               g->ctl_h->bad_count, (long long)n, g->ctl_h->first_bad));
+    // a streamed first iteration that saw only loops is Alg. 1's last one:
+    // the loop then starts afresh and stops after its one (identity) sweep
+    const bool streamed = async ? (n > 0 && m > 0) : (stream_ident && g->ctl_h->flag != 0);
     // the ordinary loop of checked sweeps (cc_run), from the streamed labels
-    st = run_impl(g, order, mode, c, async ? max_sweeps - 1 : max_sweeps, L, labels_out, out_on_device, stats, s);
+    st = run_impl(g, order, mode, c, streamed ? max_sweeps - 1 : max_sweeps, streamed ? L : nullptr, labels_out,
+                  out_on_device, stats, s);
     if (stats) {
         float ms = 0.f;
         if (cudaEventElapsedTime(&ms, ev_start, g->ev1) == cudaSuccess) stats->solve_ms = ms;
         else cudaGetLastError();  // the loop stopped before its last event: keep cc_run's time
-        if (async && n > 0 && m > 0) {
+        if (streamed) {
             stats->sweeps += 1;
-            stats->alg_bytes += 8.0 * (double)m + 4.0 * (double)n;
+            // one sweep's algorithmic bytes, counted as cc_run counts them
+            stats->alg_bytes += 8.0 * (double)m + (async ? 4.0 : 16.0) * (double)n;
         }
         stats->edges_per_s = stats->solve_ms > 0 ? (double)m / (stats->solve_ms * 1e-3) : 0.0;
     }

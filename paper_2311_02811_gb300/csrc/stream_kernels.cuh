@@ -93,4 +93,28 @@ chunk_sweep_kernel(const int32_t* __restrict__ src, const int32_t* __restrict__ 
     }
 }
 
+// Alg. 1's first iteration on one chunk after its sort (synchronous solves):
+// from L = id every chain is trivial, so each edge only lowers
+// L_u[max(w, v)] to min(w, v) (see identity_pair).  The minima commute, so
+// applying them chunk by chunk gives exactly the iteration's L_u.  target
+// starts as the identity; *flag is raised if any edge is not a loop (the
+// iteration's violation flag).
+__global__ void chunk_identity_kernel(const int32_t* __restrict__ src, const int32_t* __restrict__ dst, int64_t cnt,
+                                      int32_t* target, int32_t* flag) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    bool viol = false;
+    const int64_t q4 = cnt / 4;
+    for (int64_t g = tid; g < q4; g += stride) {
+        int32_t w[4], v[4];
+        load4(src + 4 * g, w);
+        load4(dst + 4 * g, v);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) viol |= identity_pair(w[k], v[k], target);
+    }
+    const int64_t t = 4 * q4 + tid;
+    if (t < cnt) viol |= identity_pair(__ldcs(src + t), __ldcs(dst + t), target);
+    if (__syncthreads_or(viol) && threadIdx.x == 0) *flag = 1;
+}
+
 }  // namespace cc

@@ -56,6 +56,9 @@ def test_async_labels_match_oracle(cc, family, order):
 
 @pytest.mark.parametrize("family", ["path", "components64", "grid", "rmat14"])
 def test_sync_sweeps_match_simulator(cc, family):
+    """c = 1: Alg. 1's first iteration is streamed with the upload; c = 2:
+    the chunks are only checked.  Every sweep count equals the simulator's,
+    and a run stopped after k sweeps returns the simulator's k-th state."""
     n, s, d = FAMILIES[family]()
     want, iters, conv, _ = oracle.contour_sync(n, s.numpy(), d.numpy(), 2)
     assert conv
@@ -63,6 +66,17 @@ def test_sync_sweeps_match_simulator(cc, family):
     st = cc.cc_solve_host(n, _pinned(s), _pinned(d), out, 2, cc.CC_SYNC, 1)
     assert st.sweeps == iters
     assert np.array_equal(out.numpy(), want)
+    st = cc.cc_solve_host(n, _pinned(s), _pinned(d), out, 2, cc.CC_SYNC, 2)
+    assert st.sweeps == iters + (iters % 2)
+    assert np.array_equal(out.numpy(), want)
+    for k in sorted({2, 3, iters - 1}):
+        if not 2 <= k < iters:
+            continue
+        state_k = oracle.contour_sync(n, s.numpy(), d.numpy(), 2, max_iters=k)[0]
+        rc, st = cc.cc_solve_host(n, _pinned(s), _pinned(d), out, 2, cc.CC_SYNC, 1, max_sweeps=k,
+                                  raise_on_error=False)
+        assert rc == cc.CC_ENOTCONVERGED and st.sweeps == k
+        assert np.array_equal(out.numpy(), state_k), k
 
 
 @pytest.mark.parametrize("n,m", [(1 << 21, (1 << 24) + (1 << 23) + 3), (1 << 23, (1 << 24) + (1 << 22) + 1)],
@@ -107,11 +121,14 @@ def test_edge_cases(cc):
         cc.cc_solve_host(7, e, e, out, 2, mode, 1)
         assert out.tolist() == list(range(7))
     cc.cc_solve_host(0, e, e, torch.empty(0, dtype=torch.int32), 2, cc.CC_ASYNC, 1)
-    # self-loops only
+    # self-loops only: Alg. 1 stops after its first iteration
     s = torch.tensor([3, 3, 0], dtype=torch.int32)
-    out.fill_(-1)
-    cc.cc_solve_host(7, s, s.clone(), out, 2, cc.CC_ASYNC, 1)
-    assert out.tolist() == list(range(7))
+    for mode in (cc.CC_SYNC, cc.CC_ASYNC):
+        out.fill_(-1)
+        st = cc.cc_solve_host(7, s, s.clone(), out, 2, mode, 1)
+        assert out.tolist() == list(range(7))
+        if mode == cc.CC_SYNC:
+            assert st.sweeps == 1
 
 
 def test_not_converged_leaves_a_resumable_state(cc):
